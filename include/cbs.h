@@ -1,0 +1,198 @@
+/*
+ * libcbs — complex band structure by the Sakurai-Sugiura contour-integral method,
+ * GB300-native (sm_103a).  C ABI.
+ *
+ * Method (Iwase, Futamura, Imakura, Sakurai, Ono, SC17, arXiv 1709.09347):
+ *   A crystal is cut into unit cells along the transport axis z.  Inside one cell the
+ *   real-space Kohn-Sham Hamiltonian (central finite-difference Laplacian + local
+ *   potential + separable non-local projectors) couples only to the neighbouring
+ *   cells (§2, Eq. (2)).  The Bloch ansatz psi_{n+l} = lambda^l psi_n (Eq. (3)) turns
+ *   the Kohn-Sham equation into the quadratic eigenvalue problem (Eq. (4))
+ *
+ *       P(lambda) psi = [ -lambda^{-1} H- + (E - H0) - lambda H+ ] psi = 0,
+ *
+ *   i.e. P(z) = E - H(z) with H(z) = H0 + z H+ + z^{-1} H- the cell Hamiltonian with a
+ *   twisted-periodic boundary along z.  Only lambda in the ring
+ *   lambda_min < |lambda| < 1/lambda_min (Eq. (5)) are wanted; they are found with
+ *   Algorithm 1 (§3.1) on the two-circle contour of §3.2, whose cost is the batch of
+ *   shifted solves P(z_j) Y_j = V and their duals P(z_j)^dagger Y~_j = V (Eq. (9),
+ *   (11)), done by BiCG (§3.2).
+ *
+ * Conventions for every entry point:
+ *   - complex numbers are interleaved (re, im) pairs of double (complex128) or float
+ *     (complex64);
+ *   - grid index i = ix + nx*(iy + ny*iz) (x fastest);
+ *   - a block of L vectors over the grid is stored row-major as [N][L] (the L columns
+ *     of one grid point are contiguous); a batch of such blocks is [n_sys][N][L];
+ *   - every call returns a cbs_status; nothing is thrown across the ABI;
+ *     cbs_last_error() returns a message for the calling thread's last failure;
+ *   - inputs are caller-owned and never retained; handles are library-owned and
+ *     released with the matching *_free call.
+ */
+#ifndef CBS_H
+#define CBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cbs_hamiltonian cbs_hamiltonian; /* opaque, device-resident */
+typedef struct cbs_result cbs_result;           /* opaque, host-resident   */
+
+typedef enum {
+  CBS_OK = 0,
+  CBS_EINVAL = 1,      /* bad argument or unsupported size                         */
+  CBS_ENOMEM = 2,      /* device or host allocation failed                        */
+  CBS_ECUDA = 3,       /* a CUDA runtime call failed                               */
+  CBS_ENOCONV = 4,     /* some BiCG columns hit max_iter; results are still readable */
+  CBS_EBREAKDOWN = 5,  /* BiCG breakdown (rho or (p~, Ap) vanished) in some column  */
+  CBS_ETIMEOUT = 6,    /* a bounded device-side wait gave up                        */
+  CBS_WRANK = 7        /* warning: numerical rank == L*M, eigenvalues may be missing */
+} cbs_status;
+
+enum { CBS_FP64 = 0, CBS_FP32_REFINE = 1 };     /* cbs_options.precision  */
+enum { CBS_HANKEL = 0, CBS_RR = 1 };            /* cbs_options.extraction */
+enum { CBS_C128 = 0, CBS_C64 = 1 };             /* element type of vector blocks */
+
+/* Real-space grid of one unit cell: periodic in x and y, coupled to the neighbouring
+ * cells along z.  fd_order in {2, 4, 6, 8, 10, 12}: central FD Laplacian of that order
+ * (the paper's "nine-point" FD is order 8, §4).  Needs fd_order/2 <= nz. */
+typedef struct {
+  int nx, ny, nz;
+  double hx, hy, hz;
+  int fd_order;
+} cbs_grid;
+
+/* Separable non-local projectors: V_NL = sum_a sum_{cells n} |beta_{a,n}> h_a <beta_{a,n}|.
+ * Support entries of atom a are sup_ptr[a] .. sup_ptr[a+1]-1; entry s is grid point
+ * sup_idx[s] of cell 0, covered by the copy of atom a displaced by sup_wrap[s] in
+ * {-1,0,+1} cells along z, with projector values sup_val[s*n_proj + mu] (already
+ * multiplied by sqrt(dV)).  h is [n_atoms][n_proj][n_proj], symmetric.  A grid point
+ * may appear at most once per atom (needs 2 r_c shorter than the cell along z).
+ * n_proj <= 8. */
+typedef struct {
+  int n_atoms, n_proj;
+  const int64_t *sup_ptr;
+  const int32_t *sup_idx;
+  const int8_t *sup_wrap;
+  const double *sup_val;
+  const double *h;
+} cbs_projectors;
+
+/* Two-circle contour of §3.2: radii 1/lambda_min and lambda_min, n_int points each at
+ * angles theta_j = 2 pi (j - 1/2) / n_int. */
+typedef struct {
+  double lambda_min;
+  int n_int;
+} cbs_contour;
+
+typedef struct {
+  double tol;           /* BiCG stop: ||r||/||b|| <= tol and ||r~||/||b~|| <= tol (1e-10) */
+  double delta;         /* rank cut: keep sigma_i >= delta * sigma_1 (1e-10)              */
+  double rho_max;       /* keep eigenpairs with residual rho <= rho_max (1e-8)           */
+  int max_iter;         /* BiCG iterations per column (FP64) / per inner solve (20000)   */
+  int precision;        /* CBS_FP64 or CBS_FP32_REFINE                                   */
+  int extraction;       /* CBS_HANKEL (Algorithm 1) or CBS_RR (Rayleigh-Ritz)            */
+  int check_every;      /* BiCG iterations per CUDA-graph replay between host polls (8)  */
+  double inner_tol;     /* FP32 inner solve tolerance relative to the outer residual (1e-4) */
+  int max_sweeps;       /* FP64 refinement sweeps (12)                                   */
+  int energies_per_batch; /* energies solved together; 0 = as many as fit (0)            */
+  void *stream;         /* cudaStream_t to run on; NULL = the library's own stream       */
+} cbs_options;
+
+/* Fill *opt with the defaults given above. */
+cbs_status cbs_options_default(cbs_options *opt);
+
+/* Build the device-resident Hamiltonian of one unit cell (§2, Eq. (2)).
+ * v_loc: host array of N = nx*ny*nz doubles (local potential, Ha).
+ * proj: host-side projector table, or NULL for none.
+ * Computes the FD weights, uploads V_loc and the projector table (and its transpose:
+ * for each grid point the (atom, entry) pairs that cover it), and the Frobenius norms
+ * ||H+||_F and ||H-||_F on the device.  Errors: CBS_EINVAL for inconsistent sizes
+ * (fd_order/2 > nz, a point covered twice by one atom, wrap outside {-1,0,1}, ...). */
+cbs_status cbs_create_hamiltonian(const cbs_grid *grid, const double *v_loc,
+                                  const cbs_projectors *proj, cbs_hamiltonian **out);
+void cbs_hamiltonian_free(cbs_hamiltonian *h);
+
+/* N = nx*ny*nz of the cell. */
+int64_t cbs_hamiltonian_size(const cbs_hamiltonian *h);
+
+/* ||H+||_F, ||H0 - E||_F, ||H-||_F (Frobenius) for the residual denominator. */
+cbs_status cbs_hamiltonian_norms(const cbs_hamiltonian *h, double E, double *n_plus,
+                                 double *n_zero, double *n_minus);
+
+/* The QEP matrix applied to a batch (Eq. (4)):  Y[s] = P(z_s) X[s] = E_s X[s] - H(z_s) X[s].
+ * z: host array of n_sys complex128 twists; E: host array of n_sys energies.
+ * X, Y: DEVICE pointers to [n_sys][N][L] blocks of element type dtype (CBS_C128 or
+ * CBS_C64).  1 <= L <= 1024.  Runs on `stream` (cudaStream_t, NULL = legacy default)
+ * and returns without synchronising.  Scratch is allocated per call. */
+cbs_status cbs_apply(const cbs_hamiltonian *h, int n_sys, const double *z, const double *E,
+                     int L, const void *X, void *Y, int dtype, void *stream);
+
+/* Shifted solves of §3.2 for a batch of n_sys points: BiCG on P(z_s) Y[s] = B and, as
+ * its dual, P(z_s)^dagger Yd[s] = B (= P(1/conj z_s) Yd[s] = B).
+ * z, E: host arrays [n_sys]; B: DEVICE [N][L] complex128 (shared by all systems);
+ * Y, Yd: DEVICE [n_sys][N][L] complex128 outputs; iters: host [n_sys][L] output (may be
+ * NULL): per-column iterations (FP64) or total inner iterations (FP32_REFINE).
+ * opt->precision selects plain FP64 BiCG or complex64 BiCG with FP64 refinement.
+ * Returns CBS_ENOCONV / CBS_EBREAKDOWN if some column failed (outputs still written). */
+cbs_status cbs_solve_shifted(const cbs_hamiltonian *h, int n_sys, const double *z,
+                             const double *E, int L, const void *B, void *Y, void *Yd,
+                             int *iters, const cbs_options *opt);
+
+/* Whole method for a list of energies: contour, shifted solves, moments, Hankel (or
+ * Rayleigh-Ritz) extraction, residual check, ring filter and k = -i ln(lambda)/a.
+ * energies: host [n_e]; V: [N][L] complex128 right-hand sides, host or device pointer
+ * (detected); M = N_mm moments (block Hankel of size L*M).  1 <= L, L*M <= 512.
+ * *out receives a result handle also on CBS_ENOCONV / CBS_EBREAKDOWN / CBS_WRANK. */
+cbs_status cbs_solve(const cbs_hamiltonian *h, const double *energies, int n_e,
+                     const cbs_contour *contour, int L, int M, const void *V,
+                     const cbs_options *opt, cbs_result **out);
+
+/* Per-energy results.  Eigenpairs are those with lambda_min < |lambda| < 1/lambda_min and
+ * residual <= rho_max, sorted by |lambda| then arg(lambda); vectors have unit 2-norm and
+ * their largest-modulus entry real positive. */
+int cbs_result_count(const cbs_result *r, int e);
+/* lambda, k: complex128 [count]; residual: double [count]; vectors: complex128
+ * [N][count] (may be NULL).  Caller allocates. */
+cbs_status cbs_result_get(const cbs_result *r, int e, double *lambda, double *k,
+                          double *residual, double *vectors);
+
+typedef struct {
+  int rank;             /* numerical rank m_hat of the Hankel matrix (or of S for RR)  */
+  int n_extracted;      /* eigenvalues of the reduced problem                          */
+  int n_kept;           /* eigenpairs passing the ring and residual filter             */
+  int max_iters;        /* largest BiCG iteration count over the energy's systems      */
+  int sweeps;           /* FP64 refinement sweeps (0 for plain FP64)                   */
+  int flags;            /* bit 0: not converged, bit 1: breakdown, bit 2: rank saturated */
+  double sigma_max, sigma_cut; /* sigma_1 and the smallest kept singular value          */
+  double max_solve_residual;   /* max over systems/columns of ||V - P(z)Y||/||V|| (FP64) */
+} cbs_stats;
+cbs_status cbs_result_stats(const cbs_result *r, int e, cbs_stats *st);
+
+/* All eigenvalues of the reduced problem before filtering, and their residuals.
+ * lambda: complex128 [n_extracted], residual: double [n_extracted]. */
+cbs_status cbs_result_all(const cbs_result *r, int e, double *lambda, double *residual);
+
+/* The Hankel moments mu_k = V^dagger S_k, k < 2M: complex128 [2M][L][L]. */
+cbs_status cbs_result_moments(const cbs_result *r, int e, double *mu);
+
+/* Per-column BiCG iteration counts: int [n_int][L]. */
+cbs_status cbs_result_iters(const cbs_result *r, int e, int *iters);
+
+/* Milliseconds spent in setup, solves, moments and extraction by the last cbs_solve. */
+cbs_status cbs_result_timing(const cbs_result *r, double *ms_solve, double *ms_moments,
+                             double *ms_extract, double *ms_total);
+
+void cbs_result_free(cbs_result *r);
+
+const char *cbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBS_H */

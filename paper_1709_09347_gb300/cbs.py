@@ -1,0 +1,275 @@
+"""Thin ctypes binding of libcbs (the C ABI in include/cbs.h).
+
+Argument marshalling only: every step of the method runs in libcbs's CUDA kernels.
+PyTorch provides device memory and the current stream for the device-pointer entry
+points.  There is no fallback: if libcbs.so is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcbs.so")
+
+CBS_OK, CBS_EINVAL, CBS_ENOMEM, CBS_ECUDA, CBS_ENOCONV, CBS_EBREAKDOWN, CBS_ETIMEOUT, CBS_WRANK = range(8)
+STATUS_NAMES = ["CBS_OK", "CBS_EINVAL", "CBS_ENOMEM", "CBS_ECUDA", "CBS_ENOCONV",
+                "CBS_EBREAKDOWN", "CBS_ETIMEOUT", "CBS_WRANK"]
+CBS_FP64, CBS_FP32_REFINE = 0, 1
+CBS_HANKEL, CBS_RR = 0, 1
+CBS_C128, CBS_C64 = 0, 1
+
+# every function the header declares, for the load check
+EXPORTS = (
+    "cbs_options_default", "cbs_create_hamiltonian", "cbs_hamiltonian_free", "cbs_hamiltonian_size",
+    "cbs_hamiltonian_norms", "cbs_apply", "cbs_solve_shifted", "cbs_solve", "cbs_result_count",
+    "cbs_result_get", "cbs_result_stats", "cbs_result_all", "cbs_result_moments", "cbs_result_iters",
+    "cbs_result_timing", "cbs_result_free", "cbs_last_error",
+)
+
+
+class Grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+                ("hx", ct.c_double), ("hy", ct.c_double), ("hz", ct.c_double),
+                ("fd_order", ct.c_int)]
+
+
+class Projectors(ct.Structure):
+    _fields_ = [("n_atoms", ct.c_int), ("n_proj", ct.c_int),
+                ("sup_ptr", ct.POINTER(ct.c_int64)), ("sup_idx", ct.POINTER(ct.c_int32)),
+                ("sup_wrap", ct.POINTER(ct.c_int8)), ("sup_val", ct.POINTER(ct.c_double)),
+                ("h", ct.POINTER(ct.c_double))]
+
+
+class Contour(ct.Structure):
+    _fields_ = [("lambda_min", ct.c_double), ("n_int", ct.c_int)]
+
+
+class Options(ct.Structure):
+    _fields_ = [("tol", ct.c_double), ("delta", ct.c_double), ("rho_max", ct.c_double),
+                ("max_iter", ct.c_int), ("precision", ct.c_int), ("extraction", ct.c_int),
+                ("check_every", ct.c_int), ("inner_tol", ct.c_double), ("max_sweeps", ct.c_int),
+                ("energies_per_batch", ct.c_int), ("stream", ct.c_void_p)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("rank", ct.c_int), ("n_extracted", ct.c_int), ("n_kept", ct.c_int),
+                ("max_iters", ct.c_int), ("sweeps", ct.c_int), ("flags", ct.c_int),
+                ("sigma_max", ct.c_double), ("sigma_cut", ct.c_double),
+                ("max_solve_residual", ct.c_double)]
+
+
+class CbsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libcbs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libcbs.so not found at {LIB_PATH}: build it with "
+                           "`python -m paper_1709_09347_gb300.build`")
+    lib = ct.CDLL(LIB_PATH)
+    P, I, D, V = ct.POINTER, ct.c_int, ct.c_double, ct.c_void_p
+    lib.cbs_options_default.argtypes = [P(Options)]
+    lib.cbs_create_hamiltonian.argtypes = [P(Grid), P(D), P(Projectors), P(V)]
+    lib.cbs_hamiltonian_free.argtypes = [V]
+    lib.cbs_hamiltonian_free.restype = None
+    lib.cbs_hamiltonian_size.argtypes = [V]
+    lib.cbs_hamiltonian_size.restype = ct.c_int64
+    lib.cbs_hamiltonian_norms.argtypes = [V, D, P(D), P(D), P(D)]
+    lib.cbs_apply.argtypes = [V, I, P(D), P(D), I, V, V, I, V]
+    lib.cbs_solve_shifted.argtypes = [V, I, P(D), P(D), I, V, V, V, P(I), P(Options)]
+    lib.cbs_solve.argtypes = [V, P(D), I, P(Contour), I, I, V, P(Options), P(V)]
+    lib.cbs_result_count.argtypes = [V, I]
+    lib.cbs_result_get.argtypes = [V, I, P(D), P(D), P(D), P(D)]
+    lib.cbs_result_stats.argtypes = [V, I, P(Stats)]
+    lib.cbs_result_all.argtypes = [V, I, P(D), P(D)]
+    lib.cbs_result_moments.argtypes = [V, I, P(D)]
+    lib.cbs_result_iters.argtypes = [V, I, P(I)]
+    lib.cbs_result_timing.argtypes = [V, P(D), P(D), P(D), P(D)]
+    lib.cbs_result_free.argtypes = [V]
+    lib.cbs_result_free.restype = None
+    lib.cbs_last_error.restype = ct.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status, ok=(CBS_OK,)):
+    if status not in ok:
+        raise CbsError(status, load().cbs_last_error().decode())
+    return status
+
+
+def _dptr(a, ctype=ct.c_double):
+    return a.ctypes.data_as(ct.POINTER(ctype))
+
+
+def options(**kw) -> Options:
+    o = Options()
+    load().cbs_options_default(ct.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": CBS_FP64, "fp32_refine": CBS_FP32_REFINE}[v]
+        if k == "extraction" and isinstance(v, str):
+            v = {"hankel": CBS_HANKEL, "rr": CBS_RR}[v]
+        setattr(o, k, v)
+    return o
+
+
+class Hamiltonian:
+    """Device-resident cell Hamiltonian (cbs_create_hamiltonian)."""
+
+    def __init__(self, grid, vloc, projectors=None):
+        lib = load()
+        self._keep = []
+        g = Grid(grid.nx, grid.ny, grid.nz, grid.hx, grid.hy, grid.hz, grid.fd_order)
+        v = np.ascontiguousarray(vloc, dtype=np.float64)
+        pp = None
+        if projectors is not None and projectors.n_atoms > 0:
+            P = projectors
+            arrs = (np.ascontiguousarray(P.sup_ptr, np.int64), np.ascontiguousarray(P.sup_idx, np.int32),
+                    np.ascontiguousarray(P.sup_wrap, np.int8), np.ascontiguousarray(P.sup_val, np.float64),
+                    np.ascontiguousarray(P.h, np.float64))
+            self._keep.extend(arrs)
+            pp = Projectors(P.n_atoms, P.n_proj, _dptr(arrs[0], ct.c_int64), _dptr(arrs[1], ct.c_int32),
+                            _dptr(arrs[2], ct.c_int8), _dptr(arrs[3]), _dptr(arrs[4]))
+        h = ct.c_void_p()
+        _check(lib.cbs_create_hamiltonian(ct.byref(g), _dptr(v), ct.byref(pp) if pp else None, ct.byref(h)))
+        self._h = h
+        self.grid = grid
+        self.n = int(lib.cbs_hamiltonian_size(h))
+        self._keep = []
+
+    @property
+    def handle(self):
+        return self._h
+
+    def norms(self, E):
+        a, b, c = ct.c_double(), ct.c_double(), ct.c_double()
+        _check(load().cbs_hamiltonian_norms(self._h, float(E), ct.byref(a), ct.byref(b), ct.byref(c)))
+        return a.value, b.value, c.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cbs_hamiltonian_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(torch):
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def apply(H: Hamiltonian, z, E, X):
+    """Y[s] = P(z_s) X[s] = E_s X[s] - H(z_s) X[s] for a CUDA tensor X [n_sys, N, L]
+    (complex128 or complex64).  Runs on torch's current stream."""
+    import torch
+    assert X.is_cuda and X.is_contiguous() and X.dim() == 3
+    n_sys, N, L = X.shape
+    z = np.ascontiguousarray(np.broadcast_to(np.asarray(z, complex), (n_sys,)))
+    E = np.ascontiguousarray(np.broadcast_to(np.asarray(E, float), (n_sys,)))
+    zz = np.ascontiguousarray(np.stack([z.real, z.imag], axis=1))
+    Y = torch.empty_like(X)
+    dt = {torch.complex128: CBS_C128, torch.complex64: CBS_C64}[X.dtype]
+    _check(load().cbs_apply(H.handle, n_sys, _dptr(zz), _dptr(E), L, ct.c_void_p(X.data_ptr()),
+                            ct.c_void_p(Y.data_ptr()), dt, _stream_ptr(torch)))
+    return Y
+
+
+def solve_shifted(H: Hamiltonian, z, E, B, opts: Options | None = None, allow=(CBS_OK,)):
+    """Batched primal/dual shifted solves.  B: CUDA complex128 [N, L].
+    Returns (Y, Yd, iters, status) with Y, Yd CUDA tensors [n_sys, N, L]."""
+    import torch
+    assert B.is_cuda and B.dtype == torch.complex128 and B.is_contiguous()
+    z = np.atleast_1d(np.asarray(z, complex))
+    n_sys = len(z)
+    E = np.ascontiguousarray(np.broadcast_to(np.asarray(E, float), (n_sys,)))
+    zz = np.ascontiguousarray(np.stack([z.real, z.imag], axis=1))
+    N, L = B.shape
+    Y = torch.empty((n_sys, N, L), dtype=torch.complex128, device=B.device)
+    Yd = torch.empty_like(Y)
+    iters = np.zeros((n_sys, L), np.int32)
+    o = opts or options()
+    torch.cuda.current_stream().synchronize()
+    st = _check(load().cbs_solve_shifted(H.handle, n_sys, _dptr(zz), _dptr(E), L, ct.c_void_p(B.data_ptr()),
+                                         ct.c_void_p(Y.data_ptr()), ct.c_void_p(Yd.data_ptr()),
+                                         _dptr(iters, ct.c_int), ct.byref(o)),
+                ok=tuple(allow) + (CBS_OK,))
+    return Y, Yd, iters, st
+
+
+class Result:
+    """Host-side copy of a cbs_result: per-energy dicts."""
+
+    def __init__(self, handle, n_e, N, L, M, n_int, status):
+        lib = load()
+        self.status = status
+        self.energies = []
+        for e in range(n_e):
+            cnt = lib.cbs_result_count(handle, e)
+            lam = np.zeros(cnt, complex)
+            k = np.zeros(cnt, complex)
+            rho = np.zeros(cnt)
+            vec = np.zeros((N, cnt), complex)
+            _check(lib.cbs_result_get(handle, e, _dptr(lam.view(np.float64)), _dptr(k.view(np.float64)),
+                                      _dptr(rho), _dptr(vec.view(np.float64)) if cnt else None))
+            st = Stats()
+            _check(lib.cbs_result_stats(handle, e, ct.byref(st)))
+            lam_all = np.zeros(st.n_extracted, complex)
+            res_all = np.zeros(st.n_extracted)
+            _check(lib.cbs_result_all(handle, e, _dptr(lam_all.view(np.float64)), _dptr(res_all)))
+            mu = np.zeros((2 * M, L, L), complex)
+            _check(lib.cbs_result_moments(handle, e, _dptr(mu.view(np.float64))))
+            iters = np.zeros((n_int, L), np.int32)
+            _check(lib.cbs_result_iters(handle, e, _dptr(iters, ct.c_int)))
+            self.energies.append(dict(
+                lam=lam, k=k, residual=rho, vectors=vec, rank=st.rank, n_extracted=st.n_extracted,
+                n_kept=st.n_kept, max_iters=st.max_iters, sweeps=st.sweeps, flags=st.flags,
+                sigma_max=st.sigma_max, sigma_cut=st.sigma_cut,
+                max_solve_residual=st.max_solve_residual, lam_all=lam_all, res_all=res_all,
+                mu=mu, iters=iters))
+        t = [ct.c_double() for _ in range(4)]
+        _check(lib.cbs_result_timing(handle, *[ct.byref(x) for x in t]))
+        self.ms_solve, self.ms_moments, self.ms_extract, self.ms_total = (x.value for x in t)
+
+
+def solve(H: Hamiltonian, energies, lambda_min, n_int, L, M, V, opts: Options | None = None,
+          allow=(CBS_OK, CBS_WRANK)) -> Result:
+    """The whole method for a list of energies.  V: [N, L] complex128, numpy (host) or a
+    CUDA tensor (device)."""
+    lib = load()
+    en = np.ascontiguousarray(np.atleast_1d(np.asarray(energies, float)))
+    ctr = Contour(float(lambda_min), int(n_int))
+    if isinstance(V, np.ndarray):
+        Vh = np.ascontiguousarray(V, dtype=np.complex128)
+        vptr = ct.c_void_p(Vh.ctypes.data)
+    else:
+        import torch
+        assert V.is_cuda and V.dtype == torch.complex128 and V.is_contiguous()
+        torch.cuda.current_stream().synchronize()
+        vptr = ct.c_void_p(V.data_ptr())
+    o = opts or options()
+    h = ct.c_void_p()
+    st = lib.cbs_solve(H.handle, _dptr(en), len(en), ct.byref(ctr), int(L), int(M), vptr, ct.byref(o),
+                       ct.byref(h))
+    try:
+        _check(st, ok=tuple(allow) + (CBS_OK,))
+        return Result(h, len(en), H.n, int(L), int(M), int(n_int), st)
+    finally:
+        if h:
+            lib.cbs_result_free(h)

@@ -1,0 +1,478 @@
+// Batched BiCG for the primal systems P(z_s) Y = B and their duals P(z_s)^dagger Y~ = B~.
+//
+// Paper §3.2: P(lambda)^dagger = P(1/conj lambda) and z^(2) = 1/conj z^(1), so the dual
+// of an outer-circle system is the inner-circle system, and BiCG solves both for about
+// the cost of one; every right-hand-side column is an independent BiCG run (§3.3, top
+// layer).  Per column, with (a, b) = a^dagger b:
+//     p = r + beta p,  p~ = r~ + conj(beta) p~                    (beta = 0 at the start)
+//     q = P(z) p,      q~ = P(1/conj z) p~,   alpha = (r~, r) / (p~, q)
+//     x += alpha p,  r -= alpha q,  x~ += conj(alpha) p~,  r~ -= conj(alpha) q~
+//     beta = (r~', r') / (r~, r),  stop when ||r||/||b|| <= tol and ||r~||/||b~|| <= tol.
+//
+// All systems of a batch advance together; every kernel covers [2n][N][L] (primal
+// systems then their duals).  Inner products are reduced in two deterministic levels:
+// per-block partial sums over a chunk of grid points, then one thread per (system,
+// column) adding the chunks in order.  One iteration = 6 launches (update p, apply,
+// (p~, q), alpha, update x/r, beta); `check_every` iterations are captured in a CUDA
+// graph and replayed until the device-side count of active systems reaches zero.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include "bicg.cuh"
+
+namespace cbs {
+
+template <typename R>
+__device__ __forceinline__ void block_partials(double (&acc)[4], double *part, int64_t slot) {
+  extern __shared__ double red[];  // [py][L][4]
+  const int c = threadIdx.x, ly = threadIdx.y, L = blockDim.x, py = blockDim.y;
+  for (int k = 0; k < 4; ++k) red[((int64_t)ly * L + c) * 4 + k] = acc[k];
+  __syncthreads();
+  if (ly == 0) {
+    double s[4] = {0, 0, 0, 0};
+    for (int y = 0; y < py; ++y)
+      for (int k = 0; k < 4; ++k) s[k] += red[((int64_t)y * L + c) * 4 + k];
+    for (int k = 0; k < 4; ++k) part[(slot * L + c) * 4 + k] = s[k];
+  }
+}
+
+template <typename R>
+__global__ void k_init(int n, int64_t N, int L, int chunk_pts, int n_chunks, const double2 *B,
+                       int64_t bstride, const double2 *Bd, int64_t bdstride,
+                       typename CT<R>::T *x, typename CT<R>::T *r, typename CT<R>::T *p,
+                       double *part) {
+  typedef typename CT<R>::T C;
+  const int s = blockIdx.y, chunk = blockIdx.x, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
+  double acc[4] = {0, 0, 0, 0};
+  const int64_t i0 = (int64_t)chunk * chunk_pts;
+  const int64_t i1 = min(N, i0 + chunk_pts);
+  for (int64_t i = i0 + ly; i < i1; i += py) {
+    const int64_t e = ((int64_t)s * N + i) * L + c, ed = ((int64_t)(n + s) * N + i) * L + c;
+    C b = from_d<R>(B[(int64_t)s * bstride + i * L + c]);
+    C bd = from_d<R>(Bd[(int64_t)s * bdstride + i * L + c]);
+    r[e] = b; r[ed] = bd;
+    x[e] = mk<R>(0, 0); x[ed] = mk<R>(0, 0);
+    p[e] = mk<R>(0, 0); p[ed] = mk<R>(0, 0);
+    double2 bdd = to_d(bd), bb = to_d(b);
+    acc[0] += bdd.x * bb.x + bdd.y * bb.y;   // conj(bd) * b
+    acc[1] += bdd.x * bb.y - bdd.y * bb.x;
+    acc[2] += cabs2(bb);
+    acc[3] += cabs2(bdd);
+  }
+  block_partials<R>(acc, part, (int64_t)s * n_chunks + chunk);
+}
+
+__global__ void k_reduce_init(int n, int L, int n_chunks, const double *part, double2 *rho,
+                              double2 *beta, double *nb, double *nbd, int *active, int *iters,
+                              int *flags, const int *colmask, int *sys_active, int *n_active) {
+  const int s = blockIdx.x, c = threadIdx.x;
+  const int64_t k = (int64_t)s * L + c;
+  double a[4] = {0, 0, 0, 0};
+  for (int ch = 0; ch < n_chunks; ++ch)
+    for (int q = 0; q < 4; ++q) a[q] += part[(((int64_t)s * n_chunks + ch) * L + c) * 4 + q];
+  rho[k] = make_double2(a[0], a[1]);
+  beta[k] = make_double2(0, 0);
+  nb[k] = sqrt(a[2]);
+  nbd[k] = sqrt(a[3]);
+  int act = (colmask ? colmask[k] : 1) && a[2] > 0 && a[3] > 0;
+  active[k] = act;
+  iters[k] = 0;
+  flags[k] = 0;
+  int any = __syncthreads_or(act);
+  if (c == 0) {
+    sys_active[s] = any;
+    sys_active[n + s] = any;
+    if (any) atomicAdd(n_active, 1);
+  }
+}
+
+template <typename R>
+__global__ void k_update_p(int n, int64_t N, int L, int chunk_pts, const typename CT<R>::T *r,
+                           typename CT<R>::T *p, const double2 *beta, const int *active,
+                           const int *sys_active) {
+  typedef typename CT<R>::T C;
+  const int s = blockIdx.y, chunk = blockIdx.x, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
+  if (!sys_active[s]) return;
+  const int64_t k = (int64_t)s * L + c;
+  if (!active[k]) return;
+  const C b = from_d<R>(beta[k]), bc = cconj(b);
+  const int64_t i0 = (int64_t)chunk * chunk_pts;
+  const int64_t i1 = min(N, i0 + chunk_pts);
+  for (int64_t i = i0 + ly; i < i1; i += py) {
+    const int64_t e = ((int64_t)s * N + i) * L + c, ed = ((int64_t)(n + s) * N + i) * L + c;
+    p[e] = cfma(b, p[e], r[e]);
+    p[ed] = cfma(bc, p[ed], r[ed]);
+  }
+}
+
+template <typename R>
+__global__ void k_dot_pq(int n, int64_t N, int L, int chunk_pts, int n_chunks,
+                         const typename CT<R>::T *p, const typename CT<R>::T *q, double *part,
+                         const int *sys_active) {
+  typedef typename CT<R>::T C;
+  const int s = blockIdx.y, chunk = blockIdx.x, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
+  if (!sys_active[s]) return;
+  double acc[4] = {0, 0, 0, 0};
+  const int64_t i0 = (int64_t)chunk * chunk_pts;
+  const int64_t i1 = min(N, i0 + chunk_pts);
+  R ax = 0, ay = 0;
+  for (int64_t i = i0 + ly; i < i1; i += py) {
+    const C pd = p[((int64_t)(n + s) * N + i) * L + c];
+    const C qq = q[((int64_t)s * N + i) * L + c];
+    ax += pd.x * qq.x + pd.y * qq.y;
+    ay += pd.x * qq.y - pd.y * qq.x;
+  }
+  acc[0] = ax; acc[1] = ay;
+  block_partials<R>(acc, part, (int64_t)s * n_chunks + chunk);
+}
+
+__global__ void k_reduce_alpha(int n, int L, int n_chunks, const double *part, const double2 *rho,
+                               double2 *alpha, int *active, int *flags, const int *sys_active) {
+  const int s = blockIdx.x, c = threadIdx.x;
+  if (!sys_active[s]) return;
+  const int64_t k = (int64_t)s * L + c;
+  if (!active[k]) { alpha[k] = make_double2(0, 0); return; }
+  double gx = 0, gy = 0;
+  for (int ch = 0; ch < n_chunks; ++ch) {
+    gx += part[(((int64_t)s * n_chunks + ch) * L + c) * 4 + 0];
+    gy += part[(((int64_t)s * n_chunks + ch) * L + c) * 4 + 1];
+  }
+  double2 g = make_double2(gx, gy);
+  double g2 = cabs2(g);
+  if (!(g2 > 0) || !isfinite(g2)) {
+    flags[k] |= 2;
+    active[k] = 0;
+    alpha[k] = make_double2(0, 0);
+    return;
+  }
+  alpha[k] = cdiv(rho[k], g);
+}
+
+template <typename R>
+__global__ void k_pass_b(int n, int64_t N, int L, int chunk_pts, int n_chunks,
+                         typename CT<R>::T *x, typename CT<R>::T *r, const typename CT<R>::T *p,
+                         const typename CT<R>::T *q, const double2 *alpha, const int *active,
+                         double *part, const int *sys_active) {
+  typedef typename CT<R>::T C;
+  const int s = blockIdx.y, chunk = blockIdx.x, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
+  if (!sys_active[s]) return;
+  const int64_t k = (int64_t)s * L + c;
+  const bool act = active[k];
+  const C a = from_d<R>(alpha[k]), ac = cconj(a);
+  const C na = mk<R>(-a.x, -a.y), nac = mk<R>(-a.x, a.y);
+  R s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  const int64_t i0 = (int64_t)chunk * chunk_pts;
+  const int64_t i1 = min(N, i0 + chunk_pts);
+  if (act) {
+    for (int64_t i = i0 + ly; i < i1; i += py) {
+      const int64_t e = ((int64_t)s * N + i) * L + c, ed = ((int64_t)(n + s) * N + i) * L + c;
+      x[e] = cfma(a, p[e], x[e]);
+      C rr = cfma(na, q[e], r[e]);
+      r[e] = rr;
+      x[ed] = cfma(ac, p[ed], x[ed]);
+      C rd = cfma(nac, q[ed], r[ed]);
+      r[ed] = rd;
+      s0 += rd.x * rr.x + rd.y * rr.y;
+      s1 += rd.x * rr.y - rd.y * rr.x;
+      s2 += rr.x * rr.x + rr.y * rr.y;
+      s3 += rd.x * rd.x + rd.y * rd.y;
+    }
+  }
+  double acc[4] = {(double)s0, (double)s1, (double)s2, (double)s3};
+  block_partials<R>(acc, part, (int64_t)s * n_chunks + chunk);
+}
+
+__global__ void k_reduce_beta(int n, int L, int n_chunks, const double *part, double2 *rho,
+                              double2 *beta, const double *nb, const double *nbd, int *active,
+                              int *iters, int *flags, double tol, int max_iter, int *sys_active,
+                              int *n_active) {
+  const int s = blockIdx.x, c = threadIdx.x;
+  if (!sys_active[s]) return;   // uniform per block
+  const int64_t k = (int64_t)s * L + c;
+  int act = active[k];
+  if (act) {
+    double a[4] = {0, 0, 0, 0};
+    for (int ch = 0; ch < n_chunks; ++ch)
+      for (int q = 0; q < 4; ++q) a[q] += part[(((int64_t)s * n_chunks + ch) * L + c) * 4 + q];
+    const int it = iters[k] + 1;
+    iters[k] = it;
+    const double rel = sqrt(a[2]) / nb[k], reld = sqrt(a[3]) / nbd[k];
+    const double2 rn = make_double2(a[0], a[1]);
+    if (rel <= tol && reld <= tol) {
+      act = 0;
+    } else if (!isfinite(rel) || !isfinite(reld) || !(cabs2(rn) > 0)) {
+      flags[k] |= 2;
+      act = 0;
+    } else if (it >= max_iter) {
+      flags[k] |= 1;
+      act = 0;
+    } else {
+      beta[k] = cdiv(rn, rho[k]);
+      rho[k] = rn;
+    }
+    active[k] = act;
+  }
+  if (!act) beta[k] = make_double2(0, 0);
+  int any = __syncthreads_or(act);
+  if (c == 0) {
+    sys_active[s] = any;
+    sys_active[n + s] = any;
+    if (any) atomicAdd(n_active, 1);
+  }
+}
+
+__global__ void k_twists(int n, const double2 *z, const double *E, double2 *tw, double *E2) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) {
+    double2 zz = z[s];
+    tw[s] = zz;
+    tw[n + s] = cdiv(make_double2(1.0, 0.0), cconj(zz));   // 1/conj(z): dual system (§3.2)
+    E2[s] = E[s];
+    E2[n + s] = E[s];
+  }
+}
+
+cbs_status launch_twists(int n, const double2 *z, const double *E, double2 *tw, double *E2,
+                         cudaStream_t st) {
+  k_twists<<<ceil_div(n, 128), 128, 0, st>>>(n, z, E, tw, E2);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+// ---------------------------------------------------------------- Bicg<R> members
+static int64_t align256(int64_t b) { return (b + 255) & ~(int64_t)255; }
+
+static void chunking(int64_t N, int L, int *chunk_pts, int *n_chunks) {
+  dim3 blk = col_block(L);
+  int64_t cp = (N + 127) / 128;                       // at most 128 chunks per system
+  int64_t minp = (int64_t)blk.y * 8;
+  if (cp < minp) cp = minp;
+  cp = ((cp + blk.y - 1) / blk.y) * blk.y;
+  *chunk_pts = (int)cp;
+  *n_chunks = (int)((N + cp - 1) / cp);
+}
+
+template <typename R>
+size_t Bicg<R>::bytes_needed(const HamView &H, int n, int L) {
+  int cp, nc;
+  chunking(H.n, L, &cp, &nc);
+  const int64_t vec = (int64_t)2 * n * H.n * L * sizeof(C);
+  int64_t b = 4 * align256(vec);
+  b += align256((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * sizeof(C));
+  b += align256((int64_t)2 * n * sizeof(double2)) + align256((int64_t)2 * n * sizeof(double));
+  b += 3 * align256((int64_t)n * L * sizeof(double2)) + 2 * align256((int64_t)n * L * sizeof(double));
+  b += 3 * align256((int64_t)n * L * sizeof(int)) + align256((int64_t)2 * n * sizeof(int)) + 256;
+  b += align256((int64_t)n * nc * L * 4 * sizeof(double));
+  return (size_t)b;
+}
+
+template <typename R>
+cbs_status Bicg<R>::alloc(const HamView &H_, int n_, int L_) {
+  H = H_; n = n_; L = L_; N = H.n;
+  chunking(N, L, &chunk_pts, &n_chunks);
+  bytes = bytes_needed(H, n, L);
+  cudaError_t e = cudaMalloc(&block, bytes);
+  if (e != cudaSuccess) {
+    block = nullptr;
+    set_error("cudaMalloc of the BiCG state failed (reduce energies_per_batch)");
+    return CBS_ENOMEM;
+  }
+  char *b = (char *)block;
+  auto take = [&](int64_t sz) { char *r = b; b += align256(sz); return (void *)r; };
+  const int64_t vec = (int64_t)2 * n * N * L * sizeof(C);
+  x = (C *)take(vec); r = (C *)take(vec); p = (C *)take(vec); q = (C *)take(vec);
+  D = (C *)take((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * sizeof(C));
+  tw = (double2 *)take((int64_t)2 * n * sizeof(double2));
+  E = (double *)take((int64_t)2 * n * sizeof(double));
+  rho = (double2 *)take((int64_t)n * L * sizeof(double2));
+  alpha = (double2 *)take((int64_t)n * L * sizeof(double2));
+  beta = (double2 *)take((int64_t)n * L * sizeof(double2));
+  nb = (double *)take((int64_t)n * L * sizeof(double));
+  nbd = (double *)take((int64_t)n * L * sizeof(double));
+  active = (int *)take((int64_t)n * L * sizeof(int));
+  iters = (int *)take((int64_t)n * L * sizeof(int));
+  flags = (int *)take((int64_t)n * L * sizeof(int));
+  sys_active = (int *)take((int64_t)2 * n * sizeof(int));
+  n_active = (int *)take(256);
+  part = (double *)take((int64_t)n * n_chunks * L * 4 * sizeof(double));
+  return CBS_OK;
+}
+
+template <typename R>
+void Bicg<R>::release() {
+  if (block) cudaFree(block);
+  block = nullptr;
+}
+
+template <typename R>
+cbs_status Bicg<R>::set_systems(const double2 *z, const double *Es, cudaStream_t st) {
+  return launch_twists(n, z, Es, tw, E, st);
+}
+
+static size_t red_smem(int L) {
+  dim3 b = col_block(L);
+  return (size_t)b.x * b.y * 4 * sizeof(double);
+}
+
+template <typename R>
+cbs_status Bicg<R>::init(const double2 *B, int64_t bstride, const double2 *Bd, int64_t bdstride,
+                         const int *colmask, cudaStream_t st) {
+  dim3 blk = col_block(L);
+  dim3 grd((unsigned)n_chunks, (unsigned)n, 1);
+  k_init<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, B, bstride, Bd, bdstride,
+                                          x, r, p, part);
+  CBS_CUDA(cudaGetLastError());
+  CBS_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+  k_reduce_init<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, beta, nb, nbd, active, iters, flags,
+                                 colmask, sys_active, n_active);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+template <typename R>
+cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st) {
+  dim3 blk = col_block(L);
+  dim3 grd((unsigned)n_chunks, (unsigned)n, 1);
+  k_update_p<R><<<grd, blk, 0, st>>>(n, N, L, chunk_pts, r, p, beta, active, sys_active);
+  CBS_CUDA(cudaGetLastError());
+  cbs_status s = apply_P<R>(H, 2 * n, L, p, q, tw, false, E, D, sys_active, st);
+  if (s != CBS_OK) return s;
+  k_dot_pq<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, p, q, part, sys_active);
+  CBS_CUDA(cudaGetLastError());
+  k_reduce_alpha<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, alpha, active, flags, sys_active);
+  CBS_CUDA(cudaGetLastError());
+  k_pass_b<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, x, r, p, q, alpha,
+                                             active, part, sys_active);
+  CBS_CUDA(cudaGetLastError());
+  CBS_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+  k_reduce_beta<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, beta, nb, nbd, active, iters, flags,
+                                 tol, max_iter, sys_active, n_active);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+template <typename R>
+cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStream_t st,
+                            int *host_iters_done) {
+  if (check_every < 1) check_every = 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cbs_status s = CBS_OK;
+  for (int k = 0; k < check_every && s == CBS_OK; ++k) s = step(tol, max_iter, st);
+  cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  if (s != CBS_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+  int *h_active = nullptr;
+  ce = cudaMallocHost(&h_active, sizeof(int));
+  if (ce != cudaSuccess) { cudaGraphExecDestroy(exec); return cuda_fail(ce, "cudaMallocHost"); }
+  int done = 0;
+  s = CBS_OK;
+  // every replay advances all still-active columns by check_every iterations; max_iter is
+  // also enforced per column on the device, so the loop ends within max_iter/check_every + 1
+  const int max_replays = max_iter / check_every + 2;
+  for (int rep = 0; rep < max_replays; ++rep) {
+    ce = cudaGraphLaunch(exec, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) { s = cuda_fail(ce, "BiCG graph replay"); break; }
+    done += check_every;
+    if (*h_active == 0) break;
+  }
+  cudaFreeHost(h_active);
+  cudaGraphExecDestroy(exec);
+  if (host_iters_done) *host_iters_done = done;
+  return s;
+}
+
+template struct Bicg<double>;
+template struct Bicg<float>;
+
+// ---------------------------------------------------------------- refinement helpers
+// AY holds P(z)Y (primal, systems 0..n-1) and P(z)^dagger Y~ (dual, n..2n-1); replace by
+// B - AY and record per-column squared norms.
+__global__ void k_residual(int n, int64_t N, int L, const double2 *B, int64_t bstride,
+                           const double2 *Bd, int64_t bdstride, double2 *AY, double *colnorm2) {
+  const int s2 = blockIdx.y, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
+  const bool dual = s2 >= n;
+  const int s = dual ? s2 - n : s2;
+  const double2 *b = dual ? Bd + (int64_t)s * bdstride : B + (int64_t)s * bstride;
+  double acc = 0;
+  const int64_t per = ((N + gridDim.x - 1) / gridDim.x);
+  const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(N, i0 + per);
+  for (int64_t i = i0 + ly; i < i1; i += py) {
+    const int64_t e = ((int64_t)s2 * N + i) * L + c;
+    double2 v = csub(b[i * L + c], AY[e]);
+    AY[e] = v;
+    acc += cabs2(v);
+  }
+  extern __shared__ double red1[];
+  red1[ly * L + c] = acc;
+  __syncthreads();
+  if (ly == 0) {
+    double t = 0;
+    for (int y = 0; y < py; ++y) t += red1[y * L + c];
+    colnorm2[((int64_t)s2 * gridDim.x + blockIdx.x) * L + c] = t;
+  }
+}
+
+cbs_status launch_residual(int n2, int64_t N, int L, const double2 *B, int64_t bstride,
+                           const double2 *Bd, int64_t bdstride, int n, double2 *AY,
+                           double *colnorm2, cudaStream_t st) {
+  dim3 blk = col_block(L);
+  dim3 grd(64, (unsigned)n2, 1);
+  k_residual<<<grd, blk, (size_t)blk.x * blk.y * sizeof(double), st>>>(n, N, L, B, bstride, Bd,
+                                                                        bdstride, AY, colnorm2);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+__global__ void k_accumulate(int64_t count, double2 *Y, const float2 *X) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float2 v = X[e];
+    double2 y = Y[e];
+    Y[e] = make_double2(y.x + (double)v.x, y.y + (double)v.y);
+  }
+}
+
+cbs_status launch_accumulate(int64_t count, double2 *Y, const float2 *X, cudaStream_t st) {
+  k_accumulate<<<152 * 8, 256, 0, st>>>(count, Y, X);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+}  // namespace cbs
+
+namespace cbs {
+
+// colnorm2: [2n][nchunks][L] partial squared norms of the residuals (primal then dual);
+// bnorm: [2n][L] right-hand-side norms.  colmask[s][c] = 1 if the column still needs work.
+__global__ void k_refine_check(int n, int L, int nchunks, const double *colnorm2, const double *bnorm,
+                               double tol, int *colmask, int *n_unconv, double *maxrel) {
+  const int s = blockIdx.x, c = threadIdx.x;
+  double a = 0, b = 0;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    a += colnorm2[((int64_t)s * nchunks + ch) * L + c];
+    b += colnorm2[((int64_t)(n + s) * nchunks + ch) * L + c];
+  }
+  const double nb = bnorm[(int64_t)s * L + c], nbd = bnorm[(int64_t)(n + s) * L + c];
+  const double rel = nb > 0 ? sqrt(a) / nb : 0.0, reld = nbd > 0 ? sqrt(b) / nbd : 0.0;
+  const int need = !(rel <= tol && reld <= tol);
+  colmask[(int64_t)s * L + c] = need;
+  maxrel[(int64_t)s * L + c] = fmax(rel, reld);
+  if (need) atomicAdd(n_unconv, 1);
+}
+
+cbs_status launch_refine_check(int n, int L, int nchunks, const double *colnorm2, const double *bnorm,
+                               double tol, int *colmask, int *n_unconv, double *maxrel,
+                               cudaStream_t st) {
+  k_refine_check<<<n, L, 0, st>>>(n, L, nchunks, colnorm2, bnorm, tol, colmask, n_unconv, maxrel);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+}  // namespace cbs

@@ -1,0 +1,56 @@
+// Batched BiCG for the shifted systems of §3.2 and their duals.
+#pragma once
+
+#include "common.cuh"
+
+namespace cbs {
+
+// State for n systems x L columns; the dual of system s is stored as system n + s.
+template <typename R>
+struct Bicg {
+  typedef typename CT<R>::T C;
+  HamView H;
+  int n = 0, L = 0;
+  int64_t N = 0;
+  int chunk_pts = 0, n_chunks = 0;
+  C *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;   // [2n][N][L]
+  C *D = nullptr;                                             // [2n][n_atoms][n_proj][L]
+  double2 *tw = nullptr;                                      // [2n]
+  double *E = nullptr;                                        // [2n]
+  double2 *rho = nullptr, *alpha = nullptr, *beta = nullptr;  // [n][L]
+  double *nb = nullptr, *nbd = nullptr;                       // [n][L]
+  int *active = nullptr, *iters = nullptr, *flags = nullptr;  // [n][L]
+  int *sys_active = nullptr;                                  // [2n]
+  int *n_active = nullptr;                                    // [1]
+  double *part = nullptr;                                     // [n][n_chunks][L][4]
+  void *block = nullptr;
+  size_t bytes = 0;
+
+  static size_t bytes_needed(const HamView &H, int n, int L);
+  cbs_status alloc(const HamView &H, int n, int L);
+  void release();
+  // Set twists/energies: primal twist z[s], dual twist 1/conj(z[s]); z, E on device.
+  cbs_status set_systems(const double2 *z, const double *Es, cudaStream_t st);
+  // Initialise with primal RHS B (stride bstride elements between systems, 0 = shared)
+  // and dual RHS Bd; columns with colmask == 0 (if colmask) start inactive.
+  cbs_status init(const double2 *B, int64_t bstride, const double2 *Bd, int64_t bdstride,
+                  const int *colmask, cudaStream_t st);
+  // Iterate until every column converged, broke down or reached max_iter.
+  cbs_status iterate(double tol, int max_iter, int check_every, cudaStream_t st,
+                     int *host_iters_done);
+  // one iteration (captured into graphs)
+  cbs_status step(double tol, int max_iter, cudaStream_t st);
+};
+
+// Elementwise helpers used by the refinement driver.
+// R = B - R (in place) for 2n systems, with column norms of the result into part.
+cbs_status launch_residual(int n2, int64_t N, int L, const double2 *B, int64_t bstride,
+                           const double2 *Bd, int64_t bdstride, int n, double2 *AY,
+                           double *colnorm2 /*[2n][L]*/, cudaStream_t st);
+// Y[2n] += (double) X32[2n]
+cbs_status launch_accumulate(int64_t count, double2 *Y, const float2 *X, cudaStream_t st);
+// X[2n] (type C) copies of Y (double) are not needed; zero fill helper
+cbs_status launch_twists(int n, const double2 *z, const double *E, double2 *tw, double *E2,
+                         cudaStream_t st);
+
+}  // namespace cbs

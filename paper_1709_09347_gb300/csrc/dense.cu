@@ -1,0 +1,644 @@
+// Small dense FP64 stage of Algorithm 1 (lines 2-4), on the device.
+//
+//   T = [mu_{i+j-2}], T^< = [mu_{i+j-1}]  (block Hankel, L*M square)
+//   T = U Sigma W^dagger (one-sided Jacobi SVD), rank m_hat: sigma_i >= delta sigma_1
+//   B = U_1^dagger T^< W_1 Sigma_1^{-1},  B phi = tau phi  (Hessenberg + shifted QR),
+//   lambda = tau,  psi = S W_1 Sigma_1^{-1} phi,  S = [S_0 ... S_{M-1}].
+// followed by the residual check of every in-ring pair and the filter.
+//
+// One thread block per energy runs each factorisation; matrices are column-major in
+// global memory (they fit in L2).  The GEMMs (T^< W_1, U_1^dagger C, the eigenvector
+// back-transform and S C) use a tiled complex FP64 GEMM.
+#include <math.h>
+
+#include "kernels.cuh"
+
+namespace cbs {
+
+__device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+__device__ __forceinline__ double cabsd(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 csqrt_d(double2 z) {
+  double r = hypot(z.x, z.y);
+  double re = sqrt(0.5 * (r + z.x));
+  double im = sqrt(0.5 * fmax(r - z.x, 0.0));
+  if (z.y < 0) im = -im;
+  return make_double2(re, im);
+}
+
+template <int NT>
+__device__ double block_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < NT / 32) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// ------------------------------------------------------------------ Hankel
+__global__ void k_hankel(int n_e, int L, int M, const double2 *mu, double2 *T, double2 *Tl) {
+  const int e = blockIdx.y;
+  const int n = L * M;
+  const int64_t nn = (int64_t)n * n;
+  const double2 *me = mu + (int64_t)e * 2 * M * L * L;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nn;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(idx % n), col = (int)(idx / n);
+    const int bi = row / L, r = row % L, bj = col / L, c = col % L;
+    T[e * nn + idx] = me[((int64_t)(bi + bj) * L + r) * L + c];
+    Tl[e * nn + idx] = me[((int64_t)(bi + bj + 1) * L + r) * L + c];
+  }
+}
+
+// ------------------------------------------------------------------ Jacobi SVD
+// One-sided (Hestenes) Jacobi on the columns of A (n x n, column-major), accumulating
+// the right rotations in W.  Pairs are scheduled round-robin (n/2 disjoint pairs per
+// round), one warp per pair.  On exit sigma (descending), U = A/sigma and W sorted.
+constexpr int kSvdThreads = 1024;
+__global__ void __launch_bounds__(kSvdThreads) k_svd(int n, double2 *Ab, double2 *Wb, double2 *Ub,
+                                                     double2 *Wsb, double *sigb, int *info,
+                                                     double tolj, int max_sweeps) {
+  const int e = blockIdx.x;
+  const int64_t nn = (int64_t)n * n;
+  double2 *A = Ab + e * nn, *W = Wb + e * nn, *U = Ub + e * nn, *Ws = Wsb + e * nn;
+  double *sig = sigb + (int64_t)e * n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  for (int64_t idx = tid; idx < nn; idx += blockDim.x)
+    W[idx] = make_double2((idx % n) == (idx / n) ? 1.0 : 0.0, 0.0);
+  __shared__ int rot;
+  const int nn2 = (n + 1) & ~1;   // even number of players (one dummy if n is odd)
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rot = 0;
+    __syncthreads();
+    for (int round = 0; round < nn2 - 1; ++round) {
+      for (int pi = warp; pi < nn2 / 2; pi += nwarp) {
+        // circle method: player 0 fixed, the others rotate by `round`
+        int a = pi, b = nn2 - 1 - pi;
+        int p = (a == 0) ? 0 : ((a - 1 + round) % (nn2 - 1)) + 1;
+        int q = (b == 0) ? 0 : ((b - 1 + round) % (nn2 - 1)) + 1;
+        if (p >= n || q >= n) continue;
+        double2 *ap = A + (int64_t)p * n, *aq = A + (int64_t)q * n;
+        double al = 0, be = 0, gx = 0, gy = 0;
+        for (int i = lane; i < n; i += 32) {
+          double2 u = ap[i], v = aq[i];
+          al += cabs2(u);
+          be += cabs2(v);
+          gx += u.x * v.x + u.y * v.y;   // conj(u) v
+          gy += u.x * v.y - u.y * v.x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          gx += __shfl_xor_sync(0xffffffffu, gx, o);
+          gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        }
+        const double g = hypot(gx, gy);
+        if (!(g > tolj * sqrt(al * be)) || al == 0.0 || be == 0.0) continue;
+        const double zeta = (be - al) / (2.0 * g);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        const double2 ph = make_double2(gx / g, gy / g);      // e^{i phi}
+        const double2 sp = make_double2(s * ph.x, s * ph.y);  // s e^{i phi}
+        const double2 spc = make_double2(s * ph.x, -s * ph.y);// s e^{-i phi}
+        // a_p' = c a_p - s e^{-i phi} a_q ;  a_q' = s e^{i phi} a_p + c a_q
+        for (int i = lane; i < n; i += 32) {
+          double2 u = ap[i], v = aq[i];
+          ap[i] = csub(cscale(u, c), cmul(spc, v));
+          aq[i] = cadd(cmul(sp, u), cscale(v, c));
+        }
+        double2 *wp = W + (int64_t)p * n, *wq = W + (int64_t)q * n;
+        for (int i = lane; i < n; i += 32) {
+          double2 u = wp[i], v = wq[i];
+          wp[i] = csub(cscale(u, c), cmul(spc, v));
+          wq[i] = cadd(cmul(sp, u), cscale(v, c));
+        }
+        if (lane == 0) atomicAdd(&rot, 1);
+      }
+      __syncthreads();
+    }
+    if (rot == 0) break;
+    __syncthreads();
+  }
+  if (tid == 0) info[e] = (sweep >= max_sweeps) ? 1 : 0;
+  // column norms
+  for (int j = warp; j < n; j += nwarp) {
+    double s2 = 0;
+    for (int i = lane; i < n; i += 32) s2 += cabs2(A[(int64_t)j * n + i]);
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) sig[j] = sqrt(s2);
+  }
+  __syncthreads();
+  // rank of each sigma (descending, ties by index), then scatter sorted columns
+  __shared__ int rank_of[512];
+  for (int j = tid; j < n; j += blockDim.x) {
+    double sj = sig[j];
+    int r = 0;
+    for (int k = 0; k < n; ++k) {
+      double sk = sig[k];
+      r += (sk > sj) || (sk == sj && k < j);
+    }
+    rank_of[j] = r;
+  }
+  __syncthreads();
+  for (int j = warp; j < n; j += nwarp) {
+    const int r = rank_of[j];
+    const double sj = sig[j];
+    const double inv = sj > 0 ? 1.0 / sj : 0.0;
+    for (int i = lane; i < n; i += 32) {
+      U[(int64_t)r * n + i] = cscale(A[(int64_t)j * n + i], inv);
+      Ws[(int64_t)r * n + i] = W[(int64_t)j * n + i];
+    }
+  }
+  __syncthreads();
+  // sorted singular values: write into A's first column as scratch first, then back
+  double *tmp = reinterpret_cast<double *>(A);
+  for (int j = tid; j < n; j += blockDim.x) tmp[rank_of[j]] = sig[j];
+  __syncthreads();
+  for (int j = tid; j < n; j += blockDim.x) sig[j] = tmp[j];
+}
+
+__global__ void k_rank(int n_e, int n, const double *sig, double delta, int *mhat) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_e) return;
+  const double *s = sig + (int64_t)e * n;
+  int m = 0;
+  if (s[0] > 0)
+    for (int i = 0; i < n; ++i) m += (s[i] >= delta * s[0]);
+  mhat[e] = m;
+}
+
+// ------------------------------------------------------------------ tiled ZGEMM
+// C = alpha op(A) op(B) + beta C, column-major; op: 0 = N, 1 = T, 2 = C (conj transpose).
+template <int OP>
+__device__ __forceinline__ double2 opload(const double2 *A, int64_t ld, int r, int c, int R, int Cc) {
+  if (r >= R || c >= Cc) return make_double2(0, 0);
+  if (OP == 0) return A[r + (int64_t)c * ld];
+  double2 v = A[c + (int64_t)r * ld];
+  return OP == 2 ? cconj(v) : v;
+}
+
+template <int OPA, int OPB>
+__global__ void k_zgemm(int M, int N, int K, double2 alpha, const double2 *A, int64_t lda,
+                        int64_t sA, const double2 *B, int64_t ldb, int64_t sB, double2 beta,
+                        double2 *C, int64_t ldc, int64_t sC) {
+  __shared__ double2 As[16][33];
+  __shared__ double2 Bs[16][33];
+  const int bz = blockIdx.z;
+  A += bz * sA; B += bz * sB; C += bz * sC;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
+  const int m0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
+  double2 acc[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0, 0);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int t = tid; t < 512; t += 256) {
+      int mm, kk;
+      if (OPA == 0) { mm = t % 32; kk = t / 32; } else { kk = t % 16; mm = t / 16; }
+      As[kk][mm] = opload<OPA>(A, lda, m0 + mm, k0 + kk, M, K);
+      int nn2, kb;
+      if (OPB == 0) { kb = t % 16; nn2 = t / 16; } else { nn2 = t % 32; kb = t / 32; }
+      Bs[kb][nn2] = opload<OPB>(B, ldb, k0 + kb, n0 + nn2, K, N);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double2 a0 = As[kk][tx * 2], a1 = As[kk][tx * 2 + 1];
+      double2 b0 = Bs[kk][ty * 2], b1 = Bs[kk][ty * 2 + 1];
+      acc[0][0] = cfma(a0, b0, acc[0][0]);
+      acc[0][1] = cfma(a0, b1, acc[0][1]);
+      acc[1][0] = cfma(a1, b0, acc[1][0]);
+      acc[1][1] = cfma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int r = m0 + tx * 2 + a, c = n0 + ty * 2 + b;
+      if (r < M && c < N) {
+        double2 *cp = C + r + (int64_t)c * ldc;
+        double2 v = cmul(alpha, acc[a][b]);
+        if (beta.x != 0.0 || beta.y != 0.0) v = cfma(beta, *cp, v);
+        *cp = v;
+      }
+    }
+}
+
+cbs_status zgemm(int opa, int opb, int M, int N, int K, double2 alpha, const double2 *A,
+                 int64_t lda, int64_t sA, const double2 *B, int64_t ldb, int64_t sB,
+                 double2 beta, double2 *C, int64_t ldc, int64_t sC, int batch, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || batch <= 0) return CBS_OK;
+  dim3 blk(16, 16, 1);
+  dim3 grd((unsigned)ceil_div(M, 32), (unsigned)ceil_div(N, 32), (unsigned)batch);
+#define ZG(a, b) k_zgemm<a, b><<<grd, blk, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC)
+  if (opa == 0 && opb == 0) ZG(0, 0);
+  else if (opa == 0 && opb == 1) ZG(0, 1);
+  else if (opa == 0 && opb == 2) ZG(0, 2);
+  else if (opa == 1 && opb == 0) ZG(1, 0);
+  else if (opa == 2 && opb == 0) ZG(2, 0);
+  else if (opa == 1 && opb == 1) ZG(1, 1);
+  else { set_error("zgemm: unsupported op pair"); return CBS_EINVAL; }
+#undef ZG
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+// B[:, j] *= 1/sigma_j for j < m (column scaling, B is n x m with leading dim n)
+__global__ void k_scale_cols(int n, int ldm, const int *mhat, const double *sig, double2 *B, int rows_scale) {
+  const int e = blockIdx.y;
+  const int m = mhat[e];
+  const int64_t nn = (int64_t)ldm * ldm;
+  double2 *Be = B + e * nn;
+  const double *s = sig + (int64_t)e * ldm;
+  const int64_t tot = (int64_t)n * m;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % n), c = (int)(idx / n);
+    const double inv = 1.0 / s[rows_scale ? r : c];
+    Be[r + (int64_t)c * ldm] = cscale(Be[r + (int64_t)c * ldm], inv);
+  }
+}
+
+// ------------------------------------------------------------------ eigen-solver
+// Complex upper-Hessenberg reduction (Householder) and shifted QR to Schur form
+// T = Z^dagger B Z, then eigenvectors of T by back substitution for the selected
+// eigenvalues (those strictly inside the ring), compacted into Yc (m x n_ring) and
+// transformed by Z outside this kernel.
+constexpr int kEigThreads = 512;
+__global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, double2 *Bb, double2 *Zb,
+                                                     double2 *taub, double2 *Ycb, int *nring,
+                                                     int *ringidx, double lambda_min, int *info) {
+  const int e = blockIdx.x;
+  const int m = mhat[e];
+  const int64_t nn = (int64_t)ld * ld;
+  double2 *A = Bb + e * nn, *Z = Zb + e * nn, *Yc = Ycb + e * nn;
+  double2 *tau = taub + (int64_t)e * ld;
+  int *ridx = ringidx + (int64_t)e * ld;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ double2 v[512];
+  __shared__ double shr[40];
+  __shared__ double2 sh_mu;
+  __shared__ int sh_l, sh_hi, sh_act, sh_fail;
+  if (m == 0) {
+    if (tid == 0) { nring[e] = 0; info[e] = 0; }
+    return;
+  }
+  auto Aat = [&](int i, int j) -> double2 & { return A[i + (int64_t)j * ld]; };
+  for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    Z[i + (int64_t)j * ld] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  // ---- Hessenberg reduction
+  for (int k = 0; k < m - 2; ++k) {
+    double loc = 0;
+    for (int i = k + 1 + tid; i < m; i += nt) loc += cabs2(Aat(i, k));
+    const double a2 = block_sum<kEigThreads>(loc, shr);
+    if (!(a2 > 0)) continue;
+    const double alpha = sqrt(a2);
+    const double2 x0 = Aat(k + 1, k);
+    const double ax0 = cabsd(x0);
+    const double2 ph = ax0 > 0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1, 0);
+    const double2 v0 = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
+    const double vhv = 2.0 * (a2 + alpha * ax0);
+    const double tau_h = 2.0 / vhv;
+    for (int i = k + 1 + tid; i < m; i += nt) v[i] = (i == k + 1) ? v0 : Aat(i, k);
+    __syncthreads();
+    // left: A[k+1:, k:] -= tau v (v^H A)
+    for (int j = k + tid; j < m; j += nt) {
+      double2 s = make_double2(0, 0);
+      for (int i = k + 1; i < m; ++i) s = cadd(s, cmulc(v[i], Aat(i, j)));
+      s = cscale(s, tau_h);
+      for (int i = k + 1; i < m; ++i) Aat(i, j) = csub(Aat(i, j), cmul(v[i], s));
+    }
+    __syncthreads();
+    // right: A[:, k+1:] -= tau (A v) v^H ; Z likewise
+    for (int i = tid; i < m; i += nt) {
+      double2 t = make_double2(0, 0), tz = make_double2(0, 0);
+      for (int j = k + 1; j < m; ++j) {
+        t = cfma(Aat(i, j), v[j], t);
+        tz = cfma(Z[i + (int64_t)j * ld], v[j], tz);
+      }
+      t = cscale(t, tau_h);
+      tz = cscale(tz, tau_h);
+      for (int j = k + 1; j < m; ++j) {
+        Aat(i, j) = csub(Aat(i, j), cmul(t, cconj(v[j])));
+        Z[i + (int64_t)j * ld] = csub(Z[i + (int64_t)j * ld], cmul(tz, cconj(v[j])));
+      }
+    }
+    __syncthreads();
+    for (int i = k + 2 + tid; i < m; i += nt) Aat(i, k) = make_double2(0, 0);
+    if (tid == 0) Aat(k + 1, k) = make_double2(-ph.x * alpha, -ph.y * alpha);
+    __syncthreads();
+  }
+  // ---- shifted QR (single shift, Wilkinson; exceptional shifts every 10 stalls)
+  const double eps = 2.220446049250313e-16;
+  if (tid == 0) { sh_hi = m - 1; sh_fail = 0; }
+  __syncthreads();
+  int its = 0, total = 0;
+  while (true) {
+    __syncthreads();   // everyone has read the previous decision
+    if (tid == 0) {
+      int hi = sh_hi;
+      sh_act = 0;
+      if (hi < 0) {
+        sh_act = -1;
+      } else if (hi == 0) {
+        tau[0] = Aat(0, 0);
+        sh_hi = -1;
+      } else {
+        int l = hi;
+        for (; l > 0; --l) {
+          double s = cabs1(Aat(l - 1, l - 1)) + cabs1(Aat(l, l));
+          if (s == 0) s = 1e-300;
+          if (cabs1(Aat(l, l - 1)) <= eps * s) { Aat(l, l - 1) = make_double2(0, 0); break; }
+        }
+        if (l == hi) {
+          tau[hi] = Aat(hi, hi);
+          sh_hi = hi - 1;
+          its = 0;
+        } else if (++total > 60 * m) {
+          sh_fail = 1;
+          sh_act = -1;
+        } else {
+          ++its;
+          double2 mu;
+          const double2 d = Aat(hi, hi);
+          if (its % 10 == 0) {
+            const double sub = cabs1(Aat(hi, hi - 1));
+            mu = make_double2(d.x + 0.75 * sub, d.y);
+          } else {
+            const double2 a = Aat(hi - 1, hi - 1), b = Aat(hi - 1, hi), c = Aat(hi, hi - 1);
+            const double2 half = make_double2(0.5 * (a.x - d.x), 0.5 * (a.y - d.y));
+            const double2 disc = csqrt_d(cadd(cmul(half, half), cmul(b, c)));
+            const double2 mean = make_double2(0.5 * (a.x + d.x), 0.5 * (a.y + d.y));
+            const double2 m1 = cadd(mean, disc), m2 = csub(mean, disc);
+            mu = (cabs2(csub(m1, d)) <= cabs2(csub(m2, d))) ? m1 : m2;
+          }
+          sh_mu = mu;
+          sh_l = l;
+          sh_act = 1;
+        }
+      }
+    }
+    __syncthreads();
+    const int act = sh_act;
+    if (act < 0) break;
+    if (act == 0) continue;
+    const int l = sh_l, hi = sh_hi;
+    const double2 mu = sh_mu;
+    for (int k = l; k < hi; ++k) {
+      double2 x, y;
+      if (k == l) { x = csub(Aat(l, l), mu); y = Aat(l + 1, l); }
+      else { x = Aat(k, k - 1); y = Aat(k + 1, k - 1); }
+      const double ax = cabsd(x), ay = cabsd(y);
+      const double rho = hypot(ax, ay);
+      double c;
+      double2 s;
+      if (rho == 0) { c = 1; s = make_double2(0, 0); }
+      else if (ax == 0) { c = 0; s = make_double2(y.x / ay, -y.y / ay); }   // conj(y)/|y|
+      else {
+        c = ax / rho;
+        const double2 phx = make_double2(x.x / ax, x.y / ax);
+        s = cscale(cmul(phx, cconj(y)), 1.0 / rho);
+      }
+      __syncthreads();
+      // rows k, k+1:  [a; b] <- [c a + s b; -conj(s) a + c b]
+      const int j0 = (k == l) ? l : k - 1;
+      for (int j = j0 + tid; j < m; j += nt) {
+        const double2 a = Aat(k, j), b = Aat(k + 1, j);
+        Aat(k, j) = cadd(cscale(a, c), cmul(s, b));
+        Aat(k + 1, j) = csub(cscale(b, c), cmul(cconj(s), a));
+      }
+      __syncthreads();
+      if (k > l && tid == 0) Aat(k + 1, k - 1) = make_double2(0, 0);
+      // columns k, k+1:  [u, w] <- [c u + conj(s) w, -s u + c w]
+      const int i1 = min(k + 2, hi);
+      for (int i = tid; i <= i1; i += nt) {
+        const double2 u = Aat(i, k), w = Aat(i, k + 1);
+        Aat(i, k) = cadd(cscale(u, c), cmul(cconj(s), w));
+        Aat(i, k + 1) = csub(cscale(w, c), cmul(s, u));
+      }
+      for (int i = tid; i < m; i += nt) {
+        const double2 u = Z[i + (int64_t)k * ld], w = Z[i + (int64_t)(k + 1) * ld];
+        Z[i + (int64_t)k * ld] = cadd(cscale(u, c), cmul(cconj(s), w));
+        Z[i + (int64_t)(k + 1) * ld] = csub(cscale(w, c), cmul(s, u));
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // ---- select eigenvalues strictly inside the ring
+  if (tid == 0) {
+    int cnt = 0;
+    for (int k = 0; k < m; ++k) {
+      const double r = cabsd(tau[k]);
+      if (!sh_fail && isfinite(r) && r > lambda_min && r < 1.0 / lambda_min) ridx[cnt++] = k;
+    }
+    nring[e] = cnt;
+    info[e] = sh_fail;
+  }
+  __syncthreads();
+  const int cnt = nring[e];
+  // ---- eigenvectors of the triangular T for the selected eigenvalues (thread per vector)
+  double tnorm = 0;
+  for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    if (i <= j) tnorm = fmax(tnorm, cabs1(Aat(i, j)));
+  }
+  for (int o = 16; o > 0; o >>= 1) tnorm = fmax(tnorm, __shfl_xor_sync(0xffffffffu, tnorm, o));
+  __syncthreads();
+  if ((tid & 31) == 0) shr[tid >> 5] = tnorm;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0;
+    for (int w = 0; w < nt / 32; ++w) t = fmax(t, shr[w]);
+    shr[32] = t;
+  }
+  __syncthreads();
+  const double smin = fmax(eps * shr[32], 1e-300);
+  for (int r = tid; r < cnt; r += nt) {
+    const int k = ridx[r];
+    double2 *y = Yc + (int64_t)r * ld;
+    const double2 tkk = Aat(k, k);
+    for (int i = k + 1; i < m; ++i) y[i] = make_double2(0, 0);
+    y[k] = make_double2(1, 0);
+    for (int i = k - 1; i >= 0; --i) {
+      double2 sum = Aat(i, k);
+      for (int j = i + 1; j < k; ++j) sum = cfma(Aat(i, j), y[j], sum);
+      double2 den = csub(Aat(i, i), tkk);
+      if (cabs1(den) < smin) den = make_double2(smin, 0);
+      double2 yi = cdiv(sum, den);
+      y[i] = make_double2(-yi.x, -yi.y);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ residual filter
+// Per column r of Psi (N x cnt, row-major [N][cnt]) and Res = P(tau_r) Psi:
+// stats[r] = (||psi||^2, ||res||^2, max|psi_i|, index of the first maximum)
+__global__ void k_colstats(int64_t N, int cnt, const double2 *Psi, const double2 *Res, double *stats) {
+  const int r = blockIdx.x;
+  double s1 = 0, s2 = 0, mx = -1;
+  int64_t imx = 0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    const double2 p = Psi[i * cnt + r], q = Res[i * cnt + r];
+    s1 += cabs2(p);
+    s2 += cabs2(q);
+    const double a = cabs2(p);
+    if (a > mx) { mx = a; imx = i; }
+  }
+  __shared__ double sa[256], sb[256], sm[256];
+  __shared__ int64_t si[256];
+  sa[threadIdx.x] = s1; sb[threadIdx.x] = s2; sm[threadIdx.x] = mx; si[threadIdx.x] = imx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sb[threadIdx.x] += sb[threadIdx.x + o];
+      const double m2 = sm[threadIdx.x + o];
+      const int64_t i2 = si[threadIdx.x + o];
+      if (m2 > sm[threadIdx.x] || (m2 == sm[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sm[threadIdx.x] = m2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    stats[r * 4 + 0] = sa[0];
+    stats[r * 4 + 1] = sb[0];
+    stats[r * 4 + 2] = sm[0];
+    stats[r * 4 + 3] = (double)si[0];
+  }
+}
+
+// rho_r = |tau| ||P(tau) psi|| / (||psi|| (|tau|^2 nHp + |tau| nA + nHm)); keep if rho <= rho_max;
+// order kept by (|tau|, arg tau); scale_r = conj(psi_piv)/|psi_piv| / ||psi||.
+__global__ void k_filter(int cnt, const double2 *tau_ring, const double *stats, double nHp, double nA,
+                         double nHm, double rho_max, double a_cell, const double2 *Psi, int64_t N,
+                         double *rho_all, int *n_keep, int *perm, double2 *lam_out, double2 *k_out,
+                         double *rho_out, double2 *scale_out) {
+  __shared__ int keep[512];
+  __shared__ double key1[512], key2[512];
+  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+    const double2 t = tau_ring[r];
+    const double at = hypot(t.x, t.y);
+    const double num = at * sqrt(stats[r * 4 + 1]);
+    const double den = sqrt(stats[r * 4 + 0]) * (at * at * nHp + at * nA + nHm);
+    const double rho = num / den;
+    rho_all[r] = rho;
+    keep[r] = (rho <= rho_max) && isfinite(rho);
+    key1[r] = at;
+    key2[r] = atan2(t.y, t.x);
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+    if (!keep[r]) continue;
+    int pos = 0;
+    for (int q = 0; q < cnt; ++q) {
+      if (!keep[q]) continue;
+      const bool before = key1[q] < key1[r] || (key1[q] == key1[r] && (key2[q] < key2[r] ||
+                                                (key2[q] == key2[r] && q < r)));
+      pos += before;
+    }
+    perm[pos] = r;
+    const double2 t = tau_ring[r];
+    lam_out[pos] = t;
+    const double at = key1[r];
+    k_out[pos] = make_double2(key2[r] / a_cell, -log(at) / a_cell);
+    rho_out[pos] = rho_all[r];
+    const int64_t piv = (int64_t)stats[r * 4 + 3];
+    const double2 pv = Psi[piv * cnt + r];
+    const double ap = hypot(pv.x, pv.y);
+    const double nrm = sqrt(stats[r * 4 + 0]);
+    scale_out[pos] = ap > 0 ? make_double2(pv.x / (ap * nrm), -pv.y / (ap * nrm)) : make_double2(0, 0);
+  }
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int r = 0; r < cnt; ++r) c += keep[r];
+    *n_keep = c;
+  }
+}
+
+__global__ void k_gather_vectors(int64_t N, int cnt, int nk, const double2 *Psi, const int *perm,
+                                 const double2 *scale, double2 *Out) {
+  const int64_t tot = N * nk;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / nk;
+    const int q = (int)(idx % nk);
+    Out[idx] = cmul(Psi[i * cnt + perm[q]], scale[q]);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+cbs_status launch_hankel(int n_e, int L, int M, const double2 *mu, double2 *T, double2 *Tl,
+                         cudaStream_t st) {
+  const int64_t nn = (int64_t)L * M * L * M;
+  k_hankel<<<dim3((unsigned)ceil_div(nn, 256), (unsigned)n_e, 1), 256, 0, st>>>(n_e, L, M, mu, T, Tl);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+cbs_status launch_svd(int n_e, int n, double2 *A, double2 *W, double2 *U, double2 *Ws,
+                      double *sig, int *info, cudaStream_t st) {
+  if (n > 512) { set_error("L*M must be <= 512"); return CBS_EINVAL; }
+  k_svd<<<n_e, kSvdThreads, 0, st>>>(n, A, W, U, Ws, sig, info, 1e-14, 60);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+cbs_status launch_rank(int n_e, int n, const double *sig, double delta, int *mhat, cudaStream_t st) {
+  k_rank<<<ceil_div(n_e, 64), 64, 0, st>>>(n_e, n, sig, delta, mhat);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+cbs_status launch_scale(int n_e, int rows, int ld, const int *mhat, const double *sig, double2 *B,
+                        int rows_scale, cudaStream_t st) {
+  k_scale_cols<<<dim3(64, (unsigned)n_e, 1), 256, 0, st>>>(rows, ld, mhat, sig, B, rows_scale);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+cbs_status launch_eig(int n_e, int ld, const int *mhat, double2 *B, double2 *Z, double2 *tau,
+                      double2 *Yc, int *nring, int *ringidx, double lambda_min, int *info,
+                      cudaStream_t st) {
+  if (ld > 512) { set_error("L*M must be <= 512"); return CBS_EINVAL; }
+  k_eig<<<n_e, kEigThreads, 0, st>>>(ld, mhat, B, Z, tau, Yc, nring, ringidx, lambda_min, info);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+cbs_status launch_filter(int64_t N, int cnt, const double2 *tau_ring, const double2 *Psi,
+                         const double2 *Res, double *stats, double nHp, double nA, double nHm,
+                         double rho_max, double a_cell, double *rho_all, int *n_keep, int *perm,
+                         double2 *lam_out, double2 *k_out, double *rho_out, double2 *scale_out,
+                         cudaStream_t st) {
+  if (cnt <= 0) return CBS_OK;
+  if (cnt > 512) { set_error("too many in-ring eigenvalues"); return CBS_EINVAL; }
+  k_colstats<<<cnt, 256, 0, st>>>(N, cnt, Psi, Res, stats);
+  CBS_CUDA(cudaGetLastError());
+  k_filter<<<1, 512, 0, st>>>(cnt, tau_ring, stats, nHp, nA, nHm, rho_max, a_cell, Psi, N, rho_all,
+                              n_keep, perm, lam_out, k_out, rho_out, scale_out);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+cbs_status launch_gather_vectors(int64_t N, int cnt, int nk, const double2 *Psi, const int *perm,
+                                 const double2 *scale, double2 *Out, cudaStream_t st) {
+  if (nk <= 0) return CBS_OK;
+  k_gather_vectors<<<152 * 4, 256, 0, st>>>(N, cnt, nk, Psi, perm, scale, Out);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+}  // namespace cbs

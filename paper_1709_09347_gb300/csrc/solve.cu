@@ -1,0 +1,581 @@
+// Drivers: the shifted solves (plain FP64 BiCG, or complex64 BiCG with FP64 iterative
+// refinement) and the whole method for a list of energies (Algorithm 1 on the ring
+// contour of §3.2), plus the host-side result object.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace cbs;
+
+struct cbs_energy_result {
+  std::vector<double2> lam, k, vec, lam_all, mu;
+  std::vector<double> rho, res_all;
+  std::vector<int> iters;
+  cbs_stats st;
+};
+
+struct cbs_result {
+  int n_e = 0;
+  int64_t N = 0;
+  std::vector<cbs_energy_result> e;
+  double ms_solve = 0, ms_moments = 0, ms_extract = 0, ms_total = 0;
+};
+
+namespace cbs {
+
+// Stream guard: runs on the caller's stream if given, else on a private non-blocking
+// stream (graph capture needs a non-legacy stream).
+struct StreamGuard {
+  cudaStream_t st = nullptr;
+  bool own = false;
+  cbs_status open(void *user) {
+    if (user) { st = (cudaStream_t)user; return CBS_OK; }
+    CBS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    own = true;
+    return CBS_OK;
+  }
+  ~StreamGuard() {
+    if (own && st) cudaStreamDestroy(st);
+  }
+};
+
+struct DevBuf {
+  void *p = nullptr;
+  cbs_status alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+      set_error("cudaMalloc failed (" + std::to_string(bytes) + " bytes)");
+      return CBS_ENOMEM;
+    }
+    return CBS_OK;
+  }
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  template <typename T> T *as() const { return (T *)p; }
+};
+
+#define CBS_TRY(x)                     \
+  do {                                 \
+    cbs_status _s = (x);               \
+    if (_s != CBS_OK) return _s;       \
+  } while (0)
+
+__global__ void k_expand_systems(int n_e, int n_int, const double2 *z1, const double *energies,
+                                 double2 *zs, double *Es) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n_e * n_int) {
+    zs[s] = z1[s % n_int];
+    Es[s] = energies[s / n_int];
+  }
+}
+
+__global__ void k_col_norms(int64_t N, int L, const double2 *B, double *out) {
+  const int c = threadIdx.x;
+  double a = 0;
+  for (int64_t i = 0; i < N; ++i) a += cabs2(B[i * L + c]);
+  out[c] = sqrt(a);
+}
+
+__global__ void k_bnorm_expand(int n2, int L, const double *bn, double *out) {
+  const int s = blockIdx.x, c = threadIdx.x;
+  if (s < n2) out[(int64_t)s * L + c] = bn[c];
+}
+
+__global__ void k_gather_tau(int cnt, const double2 *tau, const int *ridx, double2 *out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < cnt) out[r] = tau[ridx[r]];
+}
+
+__global__ void k_scale_rows(int rows, int cols, int64_t ld, const double *sig, double2 *B) {
+  const int64_t tot = (int64_t)rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % rows), c = (int)(idx / rows);
+    B[r + c * ld] = cscale(B[r + c * ld], 1.0 / sig[r]);
+  }
+}
+
+// True residual check of solutions Y[2n] against B (shared by all systems):
+// maxrel[s][c] = max(||B - P(z)Y||, ||B - P(z)^dagger Y~||)/||B||, colmask = needs work.
+struct ResidualCheck {
+  DevBuf buf;
+  double2 *R = nullptr;
+  double2 *D = nullptr;
+  double *cn = nullptr, *bn = nullptr, *bn2 = nullptr, *maxrel = nullptr;
+  int *colmask = nullptr, *nunc = nullptr;
+  int n = 0, L = 0;
+  int64_t N = 0;
+  cbs_status alloc(const HamView &H, int n_, int L_) {
+    n = n_; L = L_; N = H.n;
+    const size_t vec = (size_t)2 * n * N * L * sizeof(double2);
+    const size_t dsz = (size_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * sizeof(double2);
+    const size_t small = (size_t)2 * n * 64 * L * sizeof(double) + 3 * (size_t)2 * n * L * sizeof(double) +
+                         (size_t)n * L * sizeof(int) + 4096;
+    CBS_TRY(buf.alloc(vec + dsz + small + 1024));
+    char *b = buf.as<char>();
+    auto take = [&](size_t sz) { char *r = b; b += (sz + 255) & ~(size_t)255; return (void *)r; };
+    R = (double2 *)take(vec);
+    D = (double2 *)take(dsz);
+    cn = (double *)take((size_t)2 * n * 64 * L * sizeof(double));
+    bn = (double *)take((size_t)L * sizeof(double));
+    bn2 = (double *)take((size_t)2 * n * L * sizeof(double));
+    maxrel = (double *)take((size_t)n * L * sizeof(double));
+    colmask = (int *)take((size_t)n * L * sizeof(int));
+    nunc = (int *)take(256);
+    return CBS_OK;
+  }
+  // Y: [2n][N][L]; tw/E: twists [2n] and energies [2n]
+  cbs_status run(const HamView &H, const double2 *Y, const double2 *B, const double2 *tw,
+                 const double *E, double tol, cudaStream_t st, int *host_unconv) {
+    CBS_TRY(apply_P<double>(H, 2 * n, L, Y, R, tw, false, E, D, nullptr, st));
+    CBS_TRY(launch_residual(2 * n, N, L, B, 0, B, 0, n, R, cn, st));
+    k_col_norms<<<1, L, 0, st>>>(N, L, B, bn);
+    k_bnorm_expand<<<2 * n, L, 0, st>>>(2 * n, L, bn, bn2);
+    CBS_CUDA(cudaGetLastError());
+    CBS_CUDA(cudaMemsetAsync(nunc, 0, sizeof(int), st));
+    CBS_TRY(launch_refine_check(n, L, 64, cn, bn2, tol, colmask, nunc, maxrel, st));
+    if (host_unconv) {
+      CBS_CUDA(cudaMemcpyAsync(host_unconv, nunc, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaStreamSynchronize(st));
+    }
+    return CBS_OK;
+  }
+};
+
+// Shifted solves for n systems; output Y[2n][N][L] (primal then dual), per-column
+// iteration counts iters[n][L], flags[n][L], and max true residual maxrel[n][L] (host).
+struct ShiftedSolver {
+  HamView H;
+  int n = 0, L = 0;
+  DevBuf ybuf;
+  double2 *Y = nullptr;      // [2n][N][L] solutions (FP64)
+  Bicg<double> b64;
+  Bicg<float> b32;
+  ResidualCheck rc;
+  std::vector<int> iters, flags;
+  std::vector<double> maxrel;
+  int sweeps = 0;
+
+  ~ShiftedSolver() { b64.release(); b32.release(); }
+
+  static size_t bytes_per_system(const HamView &H, int L, int precision) {
+    const size_t v16 = (size_t)H.n * L * 16;
+    if (precision == CBS_FP64) return 2 * (4 * v16 + v16) + 2 * v16;   // state + residual check
+    return 2 * (4 * v16 / 2) + 2 * v16 + 2 * v16 + 2 * v16;             // f32 state, Y, R
+  }
+
+  cbs_status run(const HamView &H_, int n_, int L_, const double2 *zs, const double *Es,
+                 const double2 *B, const cbs_options &o, cudaStream_t st) {
+    H = H_; n = n_; L = L_;
+    iters.assign((size_t)n * L, 0);
+    flags.assign((size_t)n * L, 0);
+    maxrel.assign((size_t)n * L, 0.0);
+    CBS_TRY(rc.alloc(H, n, L));
+    std::vector<int> it_tmp((size_t)n * L), fl_tmp((size_t)n * L);
+    if (o.precision == CBS_FP64) {
+      CBS_TRY(b64.alloc(H, n, L));
+      CBS_TRY(b64.set_systems(zs, Es, st));
+      CBS_TRY(b64.init(B, 0, B, 0, nullptr, st));
+      int done = 0;
+      CBS_TRY(b64.iterate(o.tol, o.max_iter, o.check_every, st, &done));
+      Y = b64.x;
+      CBS_TRY(rc.run(H, Y, B, b64.tw, b64.E, o.tol, st, nullptr));
+      CBS_CUDA(cudaMemcpyAsync(iters.data(), b64.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(flags.data(), b64.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(maxrel.data(), rc.maxrel, (size_t)n * L * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaStreamSynchronize(st));
+      sweeps = 0;
+      return CBS_OK;
+    }
+    // complex64 BiCG inside FP64 iterative refinement:
+    //   R = B - P(z) Y, R~ = B - P(z)^dagger Y~  (FP64)
+    //   solve P(z) D = R, P(z)^dagger D~ = R~ in complex64 to inner_tol
+    //   Y += D, Y~ += D~  (FP64), until every column meets tol.
+    CBS_TRY(ybuf.alloc((size_t)2 * n * H.n * L * sizeof(double2)));
+    Y = ybuf.as<double2>();
+    CBS_CUDA(cudaMemsetAsync(Y, 0, (size_t)2 * n * H.n * L * sizeof(double2), st));
+    CBS_TRY(b32.alloc(H, n, L));
+    CBS_TRY(b32.set_systems(zs, Es, st));
+    sweeps = 0;
+    for (int sw = 0; sw <= o.max_sweeps; ++sw) {
+      int unconv = 0;
+      CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));
+      if (unconv == 0 || sw == o.max_sweeps) break;
+      // inner solve on the residuals (rc.R holds B - AY for primal and dual)
+      CBS_TRY(b32.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
+                       rc.colmask, st));
+      int done = 0;
+      CBS_TRY(b32.iterate(o.inner_tol, o.max_iter, o.check_every, st, &done));
+      CBS_TRY(launch_accumulate((int64_t)2 * n * H.n * L, Y, b32.x, st));
+      CBS_CUDA(cudaMemcpyAsync(it_tmp.data(), b32.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), b32.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaStreamSynchronize(st));
+      for (size_t k = 0; k < iters.size(); ++k) {
+        iters[k] += it_tmp[k];
+        flags[k] |= (fl_tmp[k] & 2);   // breakdown is sticky; max_iter in an inner solve is not
+      }
+      ++sweeps;
+    }
+    std::vector<int> mask((size_t)n * L);
+    CBS_CUDA(cudaMemcpyAsync(maxrel.data(), rc.maxrel, (size_t)n * L * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaMemcpyAsync(mask.data(), rc.colmask, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaStreamSynchronize(st));
+    for (size_t k = 0; k < mask.size(); ++k)
+      if (mask[k]) flags[k] |= 1;
+    return CBS_OK;
+  }
+};
+
+static cbs_status check_opts(const cbs_options *opt, cbs_options *o) {
+  if (opt) *o = *opt;
+  else cbs_options_default(o);
+  if (!(o->tol > 0) || !(o->delta > 0) || !(o->rho_max > 0) || o->max_iter < 1 ||
+      (o->precision != CBS_FP64 && o->precision != CBS_FP32_REFINE) ||
+      (o->extraction != CBS_HANKEL && o->extraction != CBS_RR) || !(o->inner_tol > 0) ||
+      o->max_sweeps < 0) {
+    set_error("invalid cbs_options");
+    return CBS_EINVAL;
+  }
+  if (o->check_every < 1) o->check_every = 1;
+  return CBS_OK;
+}
+
+}  // namespace cbs
+
+extern "C" cbs_status cbs_solve_shifted(const cbs_hamiltonian *h, int n_sys, const double *z,
+                                        const double *E, int L, const void *B, void *Y, void *Yd,
+                                        int *iters, const cbs_options *opt) {
+  if (!h || n_sys < 1 || !z || !E || !B || !Y || !Yd || L < 1 || L > 1024) {
+    set_error("cbs_solve_shifted: bad argument");
+    return CBS_EINVAL;
+  }
+  cbs_options o;
+  CBS_TRY(check_opts(opt, &o));
+  StreamGuard sg;
+  CBS_TRY(sg.open(o.stream));
+  cudaStream_t st = sg.st;
+  DevBuf sys;
+  CBS_TRY(sys.alloc((size_t)n_sys * (sizeof(double2) + sizeof(double)) + 256));
+  double2 *zs = sys.as<double2>();
+  double *Es = (double *)(zs + n_sys);
+  CBS_CUDA(cudaMemcpyAsync(zs, z, (size_t)n_sys * sizeof(double2), cudaMemcpyHostToDevice, st));
+  CBS_CUDA(cudaMemcpyAsync(Es, E, (size_t)n_sys * sizeof(double), cudaMemcpyHostToDevice, st));
+  ShiftedSolver S;
+  CBS_TRY(S.run(h->v, n_sys, L, zs, Es, (const double2 *)B, o, st));
+  const size_t blk = (size_t)n_sys * h->v.n * L * sizeof(double2);
+  CBS_CUDA(cudaMemcpyAsync(Y, S.Y, blk, cudaMemcpyDeviceToDevice, st));
+  CBS_CUDA(cudaMemcpyAsync(Yd, (const char *)S.Y + blk, blk, cudaMemcpyDeviceToDevice, st));
+  CBS_CUDA(cudaStreamSynchronize(st));
+  if (iters) memcpy(iters, S.iters.data(), S.iters.size() * sizeof(int));
+  int fl = 0;
+  for (int f : S.flags) fl |= f;
+  if (fl & 2) { set_error("BiCG breakdown in some column"); return CBS_EBREAKDOWN; }
+  if (fl & 1) { set_error("BiCG did not converge in some column"); return CBS_ENOCONV; }
+  return CBS_OK;
+}
+
+// ---------------------------------------------------------------------- cbs_solve
+static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, int n_e,
+                             const cbs_contour *ct, int L, int M, const void *V,
+                             const cbs_options &o, cudaStream_t st, cbs_result *res) {
+  const HamView &H = h->v;
+  const int64_t N = H.n;
+  const int n_int = ct->n_int;
+  const int nLM = L * M;
+  res->n_e = n_e;
+  res->N = N;
+  res->e.resize(n_e);
+  cudaEvent_t ev[2];
+  CBS_CUDA(cudaEventCreate(&ev[0]));
+  CBS_CUDA(cudaEventCreate(&ev[1]));
+  struct EvGuard { cudaEvent_t *e; ~EvGuard() { cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); } } evg{ev};
+  auto lap = [&](double *acc) -> cbs_status {
+    CBS_CUDA(cudaEventRecord(ev[1], st));
+    CBS_CUDA(cudaEventSynchronize(ev[1]));
+    float ms = 0;
+    CBS_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    *acc += ms;
+    CBS_CUDA(cudaEventRecord(ev[0], st));
+    return CBS_OK;
+  };
+  CBS_CUDA(cudaEventRecord(ev[0], st));
+
+  // right-hand sides on the device
+  DevBuf vbuf;
+  CBS_TRY(vbuf.alloc((size_t)N * L * sizeof(double2)));
+  double2 *dV = vbuf.as<double2>();
+  CBS_CUDA(cudaMemcpyAsync(dV, V, (size_t)N * L * sizeof(double2), cudaMemcpyDefault, st));
+  // contour
+  DevBuf cbuf;
+  CBS_TRY(cbuf.alloc((size_t)n_int * (4 * M + 1) * sizeof(double2) + (size_t)n_e * sizeof(double) + 512));
+  double2 *coef = cbuf.as<double2>();
+  double2 *z1 = coef + (size_t)n_int * 4 * M;
+  double *dE = (double *)(z1 + n_int);
+  CBS_TRY(launch_contour(n_int, M, ct->lambda_min, coef, z1, st));
+  CBS_CUDA(cudaMemcpyAsync(dE, energies, (size_t)n_e * sizeof(double), cudaMemcpyHostToDevice, st));
+
+  // energies per batch from free memory
+  size_t free_b = 0, total_b = 0;
+  CBS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const size_t per_sys = ShiftedSolver::bytes_per_system(H, L, o.precision) +
+                         (size_t)2 * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * 16 * 2;
+  const size_t per_e = per_sys * n_int + (size_t)N * nLM * 16 + (size_t)4 * nLM * nLM * 16 * 6;
+  int nb = o.energies_per_batch > 0 ? o.energies_per_batch : (int)std::max<size_t>(1, (free_b * 6 / 10) / per_e);
+  nb = std::min(nb, n_e);
+
+  cbs_status ret = CBS_OK;
+  for (int e0 = 0; e0 < n_e; e0 += nb) {
+    const int ne = std::min(nb, n_e - e0);
+    const int nsys = ne * n_int;
+    DevBuf sysb;
+    CBS_TRY(sysb.alloc((size_t)nsys * (sizeof(double2) + sizeof(double)) + 256));
+    double2 *zs = sysb.as<double2>();
+    double *Es = (double *)(zs + nsys);
+    k_expand_systems<<<ceil_div(nsys, 128), 128, 0, st>>>(ne, n_int, z1, dE + e0, zs, Es);
+    CBS_CUDA(cudaGetLastError());
+    // ---- step 1: shifted solves
+    ShiftedSolver S;
+    CBS_TRY(S.run(H, nsys, L, zs, Es, dV, o, st));
+    CBS_TRY(lap(&res->ms_solve));
+    // ---- step 2: moments
+    DevBuf mbuf;
+    const int nch = vhy_chunks(N);
+    const size_t s_bytes = (size_t)ne * N * nLM * sizeof(double2);
+    const size_t mu_bytes = (size_t)ne * 2 * M * L * L * sizeof(double2);
+    const size_t part_bytes = (size_t)2 * nsys * nch * L * L * sizeof(double2);
+    CBS_TRY(mbuf.alloc(s_bytes + mu_bytes + part_bytes + 1024));
+    double2 *Sm = mbuf.as<double2>();
+    double2 *mu = (double2 *)((char *)Sm + ((s_bytes + 255) & ~(size_t)255));
+    double2 *part = (double2 *)((char *)mu + ((mu_bytes + 255) & ~(size_t)255));
+    CBS_TRY(launch_moments(nsys, ne, n_int, M, N, L, S.Y, coef, Sm, st));
+    CBS_TRY(launch_mu(nsys, ne, n_int, M, N, L, dV, S.Y, coef, part, mu, st));
+    CBS_TRY(lap(&res->ms_moments));
+    // free the solver state before the extraction
+    S.b64.release();
+    S.b32.release();
+    // ---- step 3: extraction (Hankel SVD, reduced eigenproblem, vectors, residuals)
+    const int n = nLM;   // order of the block Hankel matrices
+    const size_t nn = (size_t)n * n;
+    DevBuf xbuf;
+    CBS_TRY(xbuf.alloc(nn * sizeof(double2) * 9 * ne + (size_t)ne * n * (sizeof(double) + 2 * sizeof(double2) + sizeof(int)) + 4096));
+    double2 *T = xbuf.as<double2>();
+    double2 *Tl = T + nn * ne, *Aw = Tl + nn * ne, *Ww = Aw + nn * ne, *U = Ww + nn * ne,
+            *Ws = U + nn * ne, *C1 = Ws + nn * ne, *Bm = C1 + nn * ne, *Z = Bm + nn * ne;
+    double2 *Yc = T;   // T is dead once copied into Aw
+    double2 *tau = Z + nn * ne;
+    double *sig = (double *)(tau + (size_t)ne * n);
+    int *ridx = (int *)(sig + (size_t)ne * n);
+    DevBuf sbuf;   // mhat[ne], nring[ne], info_svd[ne], info_eig[ne]
+    CBS_TRY(sbuf.alloc((size_t)4 * ne * sizeof(int) + 64));
+    int *small = sbuf.as<int>();
+    int *mhat = small, *nring = small + ne, *isvd = small + 2 * ne, *ieig = small + 3 * ne;
+    CBS_TRY(launch_hankel(ne, L, M, mu, T, Tl, st));
+    CBS_CUDA(cudaMemcpyAsync(Aw, T, nn * ne * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    CBS_TRY(launch_svd(ne, n, Aw, Ww, U, Ws, sig, isvd, st));
+    CBS_TRY(launch_rank(ne, n, sig, o.delta, mhat, st));
+    const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+    // C1 = T^< W (all n columns), Bm = U^dagger C1, then columns j < m_hat scaled by 1/sigma_j
+    CBS_TRY(zgemm(0, 0, n, n, n, one, Tl, n, nn, Ws, n, nn, zero, C1, n, nn, ne, st));
+    CBS_TRY(zgemm(2, 0, n, n, n, one, U, n, nn, C1, n, nn, zero, Bm, n, nn, ne, st));
+    CBS_TRY(launch_scale(ne, n, n, mhat, sig, Bm, 0, st));
+    CBS_TRY(launch_eig(ne, n, mhat, Bm, Z, tau, Yc, nring, ridx, ct->lambda_min, ieig, st));
+    std::vector<int> hsmall(4 * ne);
+    std::vector<double> hsig((size_t)ne * n);
+    std::vector<double2> htau((size_t)ne * n);
+    std::vector<double2> hmu((size_t)ne * 2 * M * L * L);
+    CBS_CUDA(cudaMemcpyAsync(hsmall.data(), small, 4 * ne * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaMemcpyAsync(hsig.data(), sig, hsig.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaMemcpyAsync(htau.data(), tau, htau.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaMemcpyAsync(hmu.data(), mu, hmu.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaStreamSynchronize(st));
+    for (int e = 0; e < ne; ++e) {
+      cbs_energy_result &R = res->e[e0 + e];
+      const double Ee = energies[e0 + e];
+      const int m = hsmall[e], cnt = hsmall[ne + e];
+      memset(&R.st, 0, sizeof(R.st));
+      R.st.rank = m;
+      R.st.n_extracted = m;
+      R.st.sigma_max = hsig[(size_t)e * n];
+      R.st.sigma_cut = m > 0 ? hsig[(size_t)e * n + m - 1] : 0.0;
+      R.lam_all.assign(htau.begin() + (size_t)e * n, htau.begin() + (size_t)e * n + m);
+      R.res_all.assign(m, NAN);
+      R.mu.assign(hmu.begin() + (size_t)e * 2 * M * L * L, hmu.begin() + (size_t)(e + 1) * 2 * M * L * L);
+      R.iters.assign((size_t)n_int * L, 0);
+      int mx = 0, fl = 0;
+      double mr = 0;
+      for (int j = 0; j < n_int; ++j)
+        for (int c = 0; c < L; ++c) {
+          const size_t k = ((size_t)e * n_int + j) * L + c;
+          R.iters[(size_t)j * L + c] = S.iters[k];
+          mx = std::max(mx, S.iters[k]);
+          fl |= S.flags[k];
+          mr = std::max(mr, S.maxrel[k]);
+        }
+      R.st.max_iters = mx;
+      R.st.sweeps = S.sweeps;
+      R.st.max_solve_residual = mr;
+      R.st.flags = (fl & 3) | (m == n ? 4 : 0) | (hsmall[2 * ne + e] ? 8 : 0) | (hsmall[3 * ne + e] ? 16 : 0);
+      if (fl & 2) ret = (ret == CBS_OK ? CBS_EBREAKDOWN : ret);
+      else if (fl & 1) ret = (ret == CBS_OK ? CBS_ENOCONV : ret);
+      else if (m == n && ret == CBS_OK) ret = CBS_WRANK;
+      if (cnt == 0) continue;
+      // vectors: P1 = Z Yc (m x cnt), rows / sigma, C2 = W_1 P1 (n x cnt), Psi^T = C2^T S^T
+      DevBuf vb;
+      const size_t psi_bytes = (size_t)N * cnt * sizeof(double2);
+      const size_t dsz = (size_t)(H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * cnt * sizeof(double2);
+      CBS_TRY(vb.alloc(2 * psi_bytes + dsz + (size_t)n * cnt * 2 * sizeof(double2) + (size_t)cnt * 256 + 8192));
+      char *p = vb.as<char>();
+      auto take = [&](size_t sz) { char *r = p; p += (sz + 255) & ~(size_t)255; return (void *)r; };
+      double2 *Psi = (double2 *)take(psi_bytes);
+      double2 *Res = (double2 *)take(psi_bytes);
+      double2 *Dd = (double2 *)take(dsz);
+      double2 *P1 = (double2 *)take((size_t)n * cnt * sizeof(double2));
+      double2 *C2 = (double2 *)take((size_t)n * cnt * sizeof(double2));
+      double2 *twr = (double2 *)take((size_t)cnt * sizeof(double2));
+      double *stats = (double *)take((size_t)cnt * 4 * sizeof(double));
+      double *rho_all = (double *)take((size_t)cnt * sizeof(double));
+      int *perm = (int *)take((size_t)cnt * sizeof(int));
+      double2 *lam_o = (double2 *)take((size_t)cnt * sizeof(double2));
+      double2 *k_o = (double2 *)take((size_t)cnt * sizeof(double2));
+      double *rho_o = (double *)take((size_t)cnt * sizeof(double));
+      double2 *scale = (double2 *)take((size_t)cnt * sizeof(double2));
+      int *nkeep = (int *)take(256);
+      double *Ed = (double *)take(256);
+      CBS_CUDA(cudaMemcpyAsync(Ed, &Ee, sizeof(double), cudaMemcpyHostToDevice, st));
+      CBS_TRY(zgemm(0, 0, m, cnt, m, one, Z + nn * e, n, 0, Yc + nn * e, n, 0, zero, P1, n, 0, 1, st));
+      k_scale_rows<<<64, 256, 0, st>>>(m, cnt, n, sig + (size_t)e * n, P1);
+      CBS_CUDA(cudaGetLastError());
+      CBS_TRY(zgemm(0, 0, n, cnt, m, one, Ws + nn * e, n, 0, P1, n, 0, zero, C2, n, 0, 1, st));
+      // Psi (row-major N x cnt) = S (row-major N x n) C2  <=>  Psi^T = C2^T S^T (column-major)
+      CBS_TRY(zgemm(1, 0, cnt, (int)N, n, one, C2, n, 0, Sm + (size_t)e * N * n, n, 0, zero, Psi, cnt, 0, 1, st));
+      k_gather_tau<<<ceil_div(cnt, 128), 128, 0, st>>>(cnt, tau + (size_t)e * n, ridx + (size_t)e * n, twr);
+      CBS_CUDA(cudaGetLastError());
+      CBS_TRY(apply_P<double>(H, 1, cnt, Psi, Res, twr, true, Ed, Dd, nullptr, st));
+      double nHp, nA, nHm;
+      cbs_hamiltonian_norms(h, Ee, &nHp, &nA, &nHm);
+      const double a_cell = h->hz * H.nz;
+      CBS_TRY(launch_filter(N, cnt, twr, Psi, Res, stats, nHp, nA, nHm, o.rho_max, a_cell, rho_all,
+                            nkeep, perm, lam_o, k_o, rho_o, scale, st));
+      int hk = 0;
+      std::vector<double> hrho(cnt);
+      std::vector<int> hridx(cnt);
+      CBS_CUDA(cudaMemcpyAsync(&hk, nkeep, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(hrho.data(), rho_all, cnt * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(hridx.data(), ridx + (size_t)e * n, cnt * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaStreamSynchronize(st));
+      for (int r = 0; r < cnt; ++r) R.res_all[hridx[r]] = hrho[r];
+      R.st.n_kept = hk;
+      R.lam.resize(hk);
+      R.k.resize(hk);
+      R.rho.resize(hk);
+      R.vec.resize((size_t)N * hk);
+      if (hk > 0) {
+        CBS_TRY(launch_gather_vectors(N, cnt, hk, Psi, perm, scale, Res, st));
+        CBS_CUDA(cudaMemcpyAsync(R.lam.data(), lam_o, hk * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaMemcpyAsync(R.k.data(), k_o, hk * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaMemcpyAsync(R.rho.data(), rho_o, hk * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaMemcpyAsync(R.vec.data(), Res, (size_t)N * hk * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaStreamSynchronize(st));
+      }
+    }
+    CBS_TRY(lap(&res->ms_extract));
+  }
+  res->ms_total = res->ms_solve + res->ms_moments + res->ms_extract;
+  return ret;
+}
+
+extern "C" cbs_status cbs_solve(const cbs_hamiltonian *h, const double *energies, int n_e,
+                                const cbs_contour *contour, int L, int M, const void *V,
+                                const cbs_options *opt, cbs_result **out) {
+  if (!out) { set_error("out is NULL"); return CBS_EINVAL; }
+  *out = nullptr;
+  if (!h || !energies || n_e < 1 || !contour || !V || L < 1 || M < 1 || L * M > 512 || L > 64 ||
+      M > 16 || contour->n_int < 1 || !(contour->lambda_min > 0 && contour->lambda_min < 1)) {
+    set_error("cbs_solve: bad argument (1 <= L <= 64, 1 <= M <= 16, L*M <= 512, 0 < lambda_min < 1)");
+    return CBS_EINVAL;
+  }
+  for (int e = 0; e < n_e; ++e)
+    if (!isfinite(energies[e])) { set_error("energies must be finite"); return CBS_EINVAL; }
+  if (cbs_hamiltonian_size(h) > (int64_t)32 * 65535) {
+    set_error("cbs_solve: grid larger than 2,097,120 points");
+    return CBS_EINVAL;
+  }
+  cbs_options o;
+  CBS_TRY(check_opts(opt, &o));
+  if (o.extraction == CBS_RR) {
+    set_error("CBS_RR extraction is not available in this build");
+    return CBS_EINVAL;
+  }
+  StreamGuard sg;
+  CBS_TRY(sg.open(o.stream));
+  cbs_result *res = new (std::nothrow) cbs_result();
+  if (!res) { set_error("host allocation failed"); return CBS_ENOMEM; }
+  cbs_status s = solve_impl(h, energies, n_e, contour, L, M, V, o, sg.st, res);
+  if (s != CBS_OK && s != CBS_ENOCONV && s != CBS_EBREAKDOWN && s != CBS_WRANK) {
+    delete res;
+    return s;
+  }
+  *out = res;
+  return s;
+}
+
+extern "C" int cbs_result_count(const cbs_result *r, int e) {
+  if (!r || e < 0 || e >= r->n_e) return -1;
+  return (int)r->e[e].lam.size();
+}
+
+extern "C" cbs_status cbs_result_get(const cbs_result *r, int e, double *lambda, double *k,
+                                     double *residual, double *vectors) {
+  if (!r || e < 0 || e >= r->n_e) { set_error("bad result/energy index"); return CBS_EINVAL; }
+  const cbs_energy_result &R = r->e[e];
+  if (lambda) memcpy(lambda, R.lam.data(), R.lam.size() * sizeof(double2));
+  if (k) memcpy(k, R.k.data(), R.k.size() * sizeof(double2));
+  if (residual) memcpy(residual, R.rho.data(), R.rho.size() * sizeof(double));
+  if (vectors) memcpy(vectors, R.vec.data(), R.vec.size() * sizeof(double2));
+  return CBS_OK;
+}
+
+extern "C" cbs_status cbs_result_stats(const cbs_result *r, int e, cbs_stats *st) {
+  if (!r || e < 0 || e >= r->n_e || !st) { set_error("bad result/energy index"); return CBS_EINVAL; }
+  *st = r->e[e].st;
+  return CBS_OK;
+}
+
+extern "C" cbs_status cbs_result_all(const cbs_result *r, int e, double *lambda, double *residual) {
+  if (!r || e < 0 || e >= r->n_e) { set_error("bad result/energy index"); return CBS_EINVAL; }
+  const cbs_energy_result &R = r->e[e];
+  if (lambda) memcpy(lambda, R.lam_all.data(), R.lam_all.size() * sizeof(double2));
+  if (residual) memcpy(residual, R.res_all.data(), R.res_all.size() * sizeof(double));
+  return CBS_OK;
+}
+
+extern "C" cbs_status cbs_result_moments(const cbs_result *r, int e, double *mu) {
+  if (!r || e < 0 || e >= r->n_e || !mu) { set_error("bad result/energy index"); return CBS_EINVAL; }
+  memcpy(mu, r->e[e].mu.data(), r->e[e].mu.size() * sizeof(double2));
+  return CBS_OK;
+}
+
+extern "C" cbs_status cbs_result_iters(const cbs_result *r, int e, int *iters) {
+  if (!r || e < 0 || e >= r->n_e || !iters) { set_error("bad result/energy index"); return CBS_EINVAL; }
+  memcpy(iters, r->e[e].iters.data(), r->e[e].iters.size() * sizeof(int));
+  return CBS_OK;
+}
+
+extern "C" cbs_status cbs_result_timing(const cbs_result *r, double *ms_solve, double *ms_moments,
+                                        double *ms_extract, double *ms_total) {
+  if (!r) { set_error("null result"); return CBS_EINVAL; }
+  if (ms_solve) *ms_solve = r->ms_solve;
+  if (ms_moments) *ms_moments = r->ms_moments;
+  if (ms_extract) *ms_extract = r->ms_extract;
+  if (ms_total) *ms_total = r->ms_total;
+  return CBS_OK;
+}
+
+extern "C" void cbs_result_free(cbs_result *r) { delete r; }

@@ -1,0 +1,73 @@
+"""P(z) X through cbs_apply against the oracle's operator (Eq. (4) with the twisted
+boundary of §2), complex128 and complex64, and the Frobenius norms."""
+import numpy as np
+import pytest
+
+from oracle.operator import CellOperator
+from paper_1709_09347_gb300 import synth
+from tests._gpu_common import need_gpu, rel_err, small_cases
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(wl, zs, Es, L, dtype):
+    torch = need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((len(zs), op.n, L)) + 1j * rng.standard_normal((len(zs), op.n, L))
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    Xd = torch.from_numpy(X).to("cuda").to(tdt).contiguous()
+    Y = cbs.apply(H, zs, Es, Xd)
+    torch.cuda.synchronize()
+    Y = Y.to(torch.complex128).cpu().numpy()
+    Xr = Xd.to(torch.complex128).cpu().numpy()     # the values the kernel saw
+    worst = 0.0
+    for s, (z, E) in enumerate(zip(zs, Es)):
+        ref = op.apply_P(z, E, Xr[s])
+        worst = max(worst, rel_err(Y[s], ref))
+    return worst
+
+
+ZS = [2.0 * np.exp(0.3j), 0.5 * np.exp(-1.2j), np.exp(2.0j), 1.7 - 0.2j]
+ES = [0.3, -0.45, 0.0, 1.1]
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_apply_small_fp64(case):
+    wl = small_cases()[case]
+    assert _run(wl, ZS, ES, wl.L, "c128") < 1e-13
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_apply_small_fp32(case):
+    wl = small_cases()[case]
+    assert _run(wl, ZS, ES, wl.L, "c64") < 3e-6
+
+
+@pytest.mark.parametrize("name,L", [("c1", 16), ("c2", 32), ("c3", 32)])
+def test_apply_full_size(name, L):
+    wl = synth.workload(name, with_rhs=False)
+    assert _run(wl, ZS[:2], ES[:2], L, "c128") < 1e-13
+    assert _run(wl, ZS[:1], ES[:1], L, "c64") < 3e-6
+
+
+@pytest.mark.parametrize("case", [0, 1, 4])
+def test_frobenius_norms(case):
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = small_cases()[case]
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    for E in (0.0, 0.37):
+        assert np.allclose(H.norms(E), op.frobenius(E), rtol=1e-12, atol=0)
+
+
+def test_frobenius_c2():
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = synth.workload("c2", with_rhs=False)
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    assert np.allclose(H.norms(-0.2), op.frobenius(-0.2), rtol=1e-11, atol=0)

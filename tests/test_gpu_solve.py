@@ -1,0 +1,127 @@
+"""Shifted solves and the whole method through the C ABI against the oracle."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import ss
+from oracle.bicg import bicg
+from oracle.contour import ring_contour
+from oracle.dense import match
+from oracle.operator import CellOperator
+from paper_1709_09347_gb300 import synth
+from tests._gpu_common import need_gpu, rel_err, small_cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("case", [0, 1, 4])
+def test_shifted_solves_vs_direct(precision, case):
+    """P(z_j) Y = V and P(z_j)^dagger Y~ = V (Eq. (9), (11)) at ring points, against a
+    sparse direct solve of the oracle's explicit P(z)."""
+    torch = need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = small_cases()[case]
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    z1, _, _, _ = ring_contour(0.5, 8)
+    zs = z1[[0, 3, 5]]
+    E = 0.2
+    B = torch.from_numpy(wl.V).to("cuda").contiguous()
+    o = cbs.options(tol=1e-12, precision=precision)
+    Y, Yd, iters, st = cbs.solve_shifted(H, zs, E, B, o)
+    Y, Yd = Y.cpu().numpy(), Yd.cpu().numpy()
+    for s, z in enumerate(zs):
+        Pz = op.P_matrix(z, E)
+        ref = spla.spsolve(Pz, wl.V)
+        refd = spla.spsolve(Pz.conj().T.tocsc(), wl.V)
+        assert rel_err(Y[s], ref) < 1e-9
+        assert rel_err(Yd[s], refd) < 1e-9
+    assert (iters > 0).all()
+
+
+def test_shifted_iterations_match_oracle():
+    """FP64 BiCG on the device follows the oracle's iteration counts (same algorithm,
+    same stopping rule) within a few iterations of rounding drift."""
+    torch = need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = small_cases()[0]
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    z = ring_contour(0.5, 16)[0][2]
+    E = -0.1
+    B = torch.from_numpy(wl.V).to("cuda").contiguous()
+    Y, Yd, iters, st = cbs.solve_shifted(H, [z], E, B, cbs.options(tol=1e-10))
+    X, Xt, it, info = bicg(lambda X: op.apply_P(z, E, X), lambda X: op.apply_P_adjoint(z, E, X),
+                           wl.V, wl.V, tol=1e-10)
+    assert np.max(np.abs(iters[0] - it)) <= 3
+    assert rel_err(Y[0].cpu().numpy(), X) < 1e-8
+
+
+def _gpu_solve(wl, energies, precision="fp64", tol=1e-12):
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    o = cbs.options(tol=tol, precision=precision)
+    return cbs.solve(H, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V, o)
+
+
+def _compare(res_gpu, ref, lam_tol):
+    assert len(res_gpu["lam"]) == len(ref.lam)
+    worst, un_f, un_r = match(res_gpu["lam"], ref.lam, lam_tol)
+    assert not un_f and not un_r, (res_gpu["lam"], ref.lam)
+    assert worst <= lam_tol
+    assert np.all(res_gpu["residual"] <= 1e-8)
+
+
+@pytest.mark.parametrize("precision,lam_tol", [("fp64", 1e-10), ("fp32_refine", 1e-9)])
+def test_solve_c1(precision, lam_tol):
+    """Whole method on the 8x8x4 cell: eigenvalue count and values against the oracle
+    run of Algorithm 1, moments mu_k against the oracle's."""
+    wl = synth.workload("c1")
+    E = float(wl.energies[0])
+    r = _gpu_solve(wl, [E], precision).energies[0]
+    op = CellOperator(wl.grid, wl.vloc, None)
+    ref = ss.ss_hankel(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12, keep_moments=True)
+    _compare(r, ref, lam_tol)
+    assert r["rank"] == ref.rank
+    assert rel_err(r["mu"], ref.mu) < 1e-8
+    # vectors: unit norm, largest entry real positive; residual recomputed by the oracle
+    V = r["vectors"]
+    assert np.allclose(np.linalg.norm(V, axis=0), 1.0, atol=1e-12)
+    norms = op.frobenius(E)
+    rr = ss.residuals(op, E, r["lam"], V, norms)
+    assert np.all(rr <= 1e-8)
+    assert np.allclose(rr, r["residual"], rtol=1e-6, atol=1e-15)
+    assert np.allclose(np.exp(1j * r["k"] * wl.grid.a), r["lam"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_solve_tiny_projectors(precision):
+    wl = synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3,
+                             L=12, M=8, n_int=32, energies=(0.2, -0.3))
+    res = _gpu_solve(wl, wl.energies, precision)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    for e, E in enumerate(wl.energies):
+        ref = ss.ss_hankel(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12)
+        _compare(res.energies[e], ref, 1e-10 if precision == "fp64" else 1e-9)
+
+
+def test_solve_c2_properties():
+    """Full 32x32x16 cell (16 energies, FP64 form): properties that hold at any size,
+    checked with the oracle's operator: every kept pair's residual, the pairing
+    lambda <-> 1/conj(lambda) inside the ring (§3.2), rank below L*M, converged solves."""
+    wl = synth.workload("c2")
+    res = _gpu_solve(wl, wl.energies[[0, 7]], "fp64", tol=1e-10)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    for e, E in enumerate(wl.energies[[0, 7]]):
+        r = res.energies[e]
+        assert r["rank"] < wl.L * wl.M
+        assert r["max_solve_residual"] <= 1e-9
+        assert len(r["lam"]) > 0
+        rr = ss.residuals(op, E, r["lam"], r["vectors"], op.frobenius(E))
+        assert np.all(rr <= 1e-8)
+        lam = r["lam"]
+        for l in lam:
+            if abs(abs(l) - 1) > 1e-6:
+                assert np.min(np.abs(lam - 1 / np.conj(l))) / abs(l) < 1e-7
