@@ -17,12 +17,14 @@ namespace cbs {
 
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 __device__ __forceinline__ double cabsd(double2 a) { return hypot(a.x, a.y); }
+// Principal square root without cancellation: the larger of |re|, |im| of the root comes
+// from sqrt((r + |x|)/2) and the other from y / (2 t).
 __device__ __forceinline__ double2 csqrt_d(double2 z) {
-  double r = hypot(z.x, z.y);
-  double re = sqrt(0.5 * (r + z.x));
-  double im = sqrt(0.5 * fmax(r - z.x, 0.0));
-  if (z.y < 0) im = -im;
-  return make_double2(re, im);
+  if (z.x == 0.0 && z.y == 0.0) return make_double2(0.0, 0.0);
+  const double r = hypot(z.x, z.y);
+  const double t = sqrt(0.5 * (r + fabs(z.x)));
+  if (z.x >= 0.0) return make_double2(t, z.y / (2.0 * t));
+  return make_double2(fabs(z.y) / (2.0 * t), copysign(t, z.y));
 }
 
 template <int NT>

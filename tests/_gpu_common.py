@@ -33,7 +33,7 @@ def small_cases():
     every supported FD half-width that fits, with and without projectors."""
     return [
         synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3, L=8),
-        synth.tiny_workload(nx=7, ny=3, nz=5, h=0.4, fd_order=8, n_atoms=3, r_c=0.75, sigma=0.3, L=5),
+        synth.tiny_workload(nx=7, ny=4, nz=5, h=0.4, fd_order=8, n_atoms=3, r_c=0.75, sigma=0.3, L=5),
         synth.tiny_workload(nx=9, ny=11, nz=4, h=0.5, fd_order=2, n_atoms=0, projectors=False, L=3),
         synth.tiny_workload(nx=3, ny=4, nz=2, h=0.5, fd_order=4, n_atoms=1, r_c=0.45, sigma=0.2, L=1),
         synth.tiny_workload(nx=13, ny=10, nz=6, h=0.4, fd_order=12, n_atoms=4, r_c=1.1, sigma=0.4, L=33),
