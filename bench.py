@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark: CBS energies per second at eigenpair residual <= 1e-8, on GB300.
+
+One step = the whole method (contour, batched shifted BiCG solves with their duals,
+moments, Hankel SVD + reduced eigenproblem, residual filter, k) for every energy of the
+workload, through libcbs's C ABI.  Default workload: the 32x32x16 molecular-crystal
+cell (8th-order FD, 40 atoms with 4 projectors each, 16 energies in [-0.5, 0.5] Ha,
+N_int = 32 per circle, L = 32, M = 8) in plain FP64 — the configuration the metric is
+quoted on.  The complex64 + FP64-refinement form is measured on the same workload and
+reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own copy of the
+energy list (independent problems, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CBS energies/sec at residual<=1e-8 (FP32+refine vs FP64); SpMM HBM GB/s"
+UNIT = "energies/s"
+
+# DRAM traffic of the FP64 stencil+projector apply per complex output, from one ncu
+# capture (profiles/apply_fp64_c2.md), valid while csrc/apply.cu hashes to APPLY_SHA.
+APPLY_TRAFFIC = {"sha": None, "c128_bytes_per_output": None, "c64_bytes_per_output": None}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# GB300 FP64: 1.25 TFLOP/s nominal (152 SMs x 2.07 GHz x 4 FLOP/clk/SM).
+FP64_PEAK_TFLOPS = 1.25
+
+
+def _apply_sha():
+    with open(os.path.join(ROOT, "paper_1709_09347_gb300", "csrc", "apply.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def flops_per_output(wl):
+    """Algorithmic real flops per complex output of the operator apply: 2 (diagonal) +
+    18 per FD half-width step (x, y, z pairs) + 4 (E x - acc) + per covering projector
+    entry 4*n_proj (gather) + 4*n_proj + 2 (scatter)."""
+    m = wl.grid.fd_order // 2
+    f = 2 + 18 * m + 4
+    if wl.projectors is not None:
+        npj = wl.projectors.n_proj
+        f += wl.projectors.nnz / wl.grid.n * (8 * npj + 2)
+    return f
+
+
+def bytes_per_output(wl, s):
+    """Algorithmic bytes per complex output: read X and write Y once (2 s) plus the local
+    potential (s/2 per point) and the projector table (values + index) amortised over L."""
+    b = 2 * s + (s / 2) / wl.L
+    if wl.projectors is not None:
+        npj = wl.projectors.n_proj
+        b += wl.projectors.nnz / wl.grid.n * (npj * s / 2 + 8) / wl.L
+    return b
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_sample(workload: str, n_points: int, energy_index: int) -> dict:
+    """Time the oracle (as it stands) on a bounded sample: n_points of the n_int
+    quadrature-point BiCG solves of one energy, single-threaded.  Runs in a child process
+    with one BLAS/OpenMP thread so that `cores` is exact."""
+    code = f"""
+import json, os, sys, time
+sys.path.insert(0, {ROOT!r})
+from paper_1709_09347_gb300 import synth
+from oracle.operator import CellOperator
+from oracle.contour import ring_contour
+from oracle.bicg import bicg
+wl = synth.workload({workload!r})
+op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+E = float(wl.energies[{energy_index}])
+z1 = ring_contour(wl.lambda_min, wl.n_int)[0]
+t = time.time()
+iters = []
+for j in range({n_points}):
+    z = z1[j * (wl.n_int // {n_points})]
+    X, Xt, it, info = bicg(lambda X: op.apply_P(z, E, X), lambda X: op.apply_P_adjoint(z, E, X),
+                           wl.V, wl.V, tol=wl.tol)
+    iters.append(int(it.max()))
+dt = time.time() - t
+print(json.dumps(dict(seconds=dt, iters=iters, n_int=wl.n_int)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    per_energy = r["seconds"] * r["n_int"] / n_points
+    return {"value": 1.0 / per_energy, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{workload}: {n_points} of {r['n_int']} quadrature-point BiCG solves "
+                       f"(primal+dual, all L columns) at energy index {energy_index}, "
+                       f"{r['seconds']:.1f} s, iterations {r['iters']}; scaled by n_int/{n_points} "
+                       f"to one energy (extraction not included)"),
+            "seconds": r["seconds"]}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    steps = []
+    samples = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline_sample(args.workload, 1, 7)
+        if k >= args.warmup:
+            steps.append(1.0 / r["value"])
+            samples.append(r)
+    per_energy = sum(steps) / len(steps)
+    value = 1.0 / per_energy
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_energy * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "sample": "1 of n_int quadrature-point solves per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": samples[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = _dist()
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1709_09347_gb300 import cbs, synth
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = synth.workload(args.workload)
+    energies = wl.energies
+    n_e = len(energies)
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    Vd = torch.from_numpy(wl.V).to(dev).contiguous()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world > 1:
+            t = torch.tensor([x], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    def one_step(precision, profile=True):
+        o = cbs.options(precision=precision, tol=wl.tol, delta=wl.delta, profile=1 if profile else 0)
+        return cbs.solve(H, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, Vd, o)
+
+    def timed(precision, steps, warmup):
+        for _ in range(warmup):
+            one_step(precision)
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = cbs.kernel_launches()
+        results = []
+        with ClockSampler(local) as clk:
+            ev0.record()
+            for _ in range(steps):
+                results.append(one_step(precision))
+            ev1.record()
+            torch.cuda.synchronize()
+        launches = cbs.kernel_launches() - l0
+        barrier()
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        return ms, results, clk.summary(), launches
+
+    ms, results, clocks, launches = timed("fp64", args.steps, args.warmup)
+    value = args.steps * n_e * world / (ms / 1e3)
+
+    # eigenpair bookkeeping of the timed steps
+    last = results[-1]
+    kept = [len(e["lam"]) for e in last.energies]
+    worst_res = max([float(np.max(e["residual"])) for e in last.energies if len(e["residual"])] or [0.0])
+    flags = sorted({e["flags"] for e in last.energies})
+    prof = {k: sum(r.profile[k][f] for r in results) for k in ("c128",) for f in ("ms",)}
+    p128 = {f: sum(r.profile["c128"][f] for r in results) for f in ("ms", "launches", "outputs")}
+    flops = flops_per_output(wl)
+    achieved_tflops = p128["outputs"] * flops / (p128["ms"] / 1e3) / 1e12 if p128["ms"] else None
+    sha = _apply_sha()
+    traffic = None
+    if APPLY_TRAFFIC["sha"] == sha and APPLY_TRAFFIC["c128_bytes_per_output"]:
+        traffic = APPLY_TRAFFIC["c128_bytes_per_output"] * p128["outputs"] / p128["launches"]
+    roofline = {
+        "kernel": "k_apply_zm<double> (+k_proj_gather<double>): stencil + projector apply, FP64",
+        "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved_tflops / FP64_PEAK_TFLOPS if achieved_tflops else None,
+        "traffic": traffic, "peak_source": "nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
+        "flops_per_output": flops, "outputs": p128["outputs"], "launches": p128["launches"],
+        "avg_launch_ms": p128["ms"] / max(p128["launches"], 1),
+        "share_of_step": p128["ms"] / ms if ms else None,
+    }
+
+    # complex64 BiCG + FP64 refinement on the same workload
+    mixed = None
+    if not args.no_mixed:
+        ms2, res2, clocks2, launches2 = timed("fp32_refine", args.steps, 1)
+        hbm, hbm_src = _peaks()
+        p64 = {f: sum(r.profile["c64"][f] for r in res2) for f in ("ms", "launches", "outputs")}
+        bpo = bytes_per_output(wl, 8)
+        ach = p64["outputs"] * bpo / (p64["ms"] / 1e3) / 1e9 if p64["ms"] else None
+        kept2 = [len(e["lam"]) for e in res2[-1].energies]
+        mixed = {
+            "value": args.steps * n_e * world / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / args.steps,
+            "dtype": "c64 BiCG + f64 refinement", "kept_per_energy": kept2,
+            "same_count_as_fp64": kept2 == kept,
+            "max_residual": max([float(np.max(e["residual"])) for e in res2[-1].energies if len(e["residual"])] or [0.0]),
+            "roofline": {"kernel": "k_apply_zm<float> (+k_proj_gather<float>): stencil + projector apply, complex64",
+                         "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm if ach else None, "traffic": None,
+                         "peak_source": hbm_src, "bytes_per_output": bpo,
+                         "avg_launch_ms": p64["ms"] / max(p64["launches"], 1)},
+            "clocks": clocks2, "gpu_launches": launches2,
+        }
+
+    # end to end through the C ABI with host buffers: Hamiltonian upload, V upload,
+    # solve, results (eigenvalues, k, residuals, eigenvectors) back to the host
+    def e2e_step():
+        Hh = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+        r = cbs.solve(Hh, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                      cbs.options(precision="fp64", tol=wl.tol, delta=wl.delta))
+        Hh.close()
+        return r
+    e2e_steps = 1
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r_e2e = e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    h2d = wl.vloc.nbytes + wl.V.nbytes
+    if wl.projectors is not None:
+        P = wl.projectors
+        h2d += P.sup_ptr.nbytes + P.sup_idx.nbytes + P.sup_wrap.nbytes + P.sup_val.nbytes + P.h.nbytes
+    d2h = sum(e["lam"].nbytes + e["k"].nbytes + e["residual"].nbytes + e["vectors"].nbytes
+              for e in r_e2e.energies)
+    e2e = {"value": e2e_steps * n_e * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline_sample(args.workload, 2, 7)
+        except Exception as ex:  # noqa: BLE001
+            cpu = {"error": str(ex)[-300:]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl.grid.nx}x{wl.grid.ny}x{wl.grid.nz} cell, "
+                                   f"FD{wl.grid.fd_order}, "
+                                   f"{wl.projectors.n_atoms if wl.projectors else 0} atoms x 4 projectors, "
+                                   f"{n_e} energies, N_int={wl.n_int}, L={wl.L}, M={wl.M}, "
+                                   f"lambda_min={wl.lambda_min}, BiCG tol {wl.tol:g}, plain FP64",
+                       "energies_per_step": n_e, "l2": "state per step >> L2 (no flush needed)",
+                       "kept_per_energy": kept, "max_residual": worst_res, "flags": flags},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+            "cpu_baseline": cpu, "fp32_refine": mixed,
+            "stage_ms_last_step": {"solve": last.ms_solve, "moments": last.ms_moments,
+                                   "extract": last.ms_extract},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -100,6 +100,7 @@ typedef struct {
   double inner_tol;     /* FP32 inner solve tolerance relative to the outer residual (1e-4) */
   int max_sweeps;       /* FP64 refinement sweeps (12)                                   */
   int energies_per_batch; /* energies solved together; 0 = as many as fit (0)            */
+  int profile;          /* 1: time every operator-apply launch with CUDA events (0)      */
   void *stream;         /* cudaStream_t to run on; NULL = the library's own stream       */
 } cbs_options;
 
@@ -127,8 +128,8 @@ cbs_status cbs_hamiltonian_norms(const cbs_hamiltonian *h, double E, double *n_p
 /* The QEP matrix applied to a batch (Eq. (4)):  Y[s] = P(z_s) X[s] = E_s X[s] - H(z_s) X[s].
  * z: host array of n_sys complex128 twists; E: host array of n_sys energies.
  * X, Y: DEVICE pointers to [n_sys][N][L] blocks of element type dtype (CBS_C128 or
- * CBS_C64).  1 <= L <= 1024.  Runs on `stream` (cudaStream_t, NULL = legacy default)
- * and returns without synchronising.  Scratch is allocated per call. */
+ * CBS_C64).  1 <= L <= 1024.  Runs on `stream` (cudaStream_t, NULL = legacy default);
+ * scratch is allocated per call and freed after synchronising that stream. */
 cbs_status cbs_apply(const cbs_hamiltonian *h, int n_sys, const double *z, const double *E,
                      int L, const void *X, void *Y, int dtype, void *stream);
 
@@ -187,9 +188,20 @@ cbs_status cbs_result_iters(const cbs_result *r, int e, int *iters);
 cbs_status cbs_result_timing(const cbs_result *r, double *ms_solve, double *ms_moments,
                              double *ms_extract, double *ms_total);
 
+/* Operator-apply (stencil + projector) launches of the last cbs_solve with profile = 1:
+ * total device milliseconds, number of launches and number of complex outputs written
+ * (active systems x N x L summed over launches), for element type dtype (CBS_C128 or
+ * CBS_C64).  All zero when profiling was off. */
+cbs_status cbs_result_profile(const cbs_result *r, int dtype, double *ms, double *launches,
+                              double *outputs);
+
 void cbs_result_free(cbs_result *r);
 
 const char *cbs_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far; a CUDA-graph
+ * replay counts each of its kernel nodes. */
+uint64_t cbs_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -83,6 +83,7 @@ class CellOperator:
                     if np.any(sel):
                         add(b, idx[sel], col[sel], wz)
         self.K = {}
+        self.BT = {}
         for b in (-1, 0, 1):
             if rows[b]:
                 r = np.concatenate(rows[b])
@@ -106,6 +107,7 @@ class CellOperator:
                 v = P.sup_val[sel].ravel()
                 self.B[mm] = sp.csr_matrix((v, (r, cc)), shape=(N, P.n_atoms * npj))
             self.Hblk = sp.block_diag([sp.csr_matrix(P.h[a]) for a in range(P.n_atoms)], format="csr")
+            self.BT = {mm: B.T.tocsr() for mm, B in self.B.items()}
         else:
             self.Hblk = None
 
@@ -134,10 +136,11 @@ class CellOperator:
         """H(z) X = H0 X + z Hp X + z^{-1} Hm X  (twisted-periodic cell Hamiltonian)."""
         Y = self.K[0] @ X + z * (self.K[1] @ X) + (1.0 / z) * (self.K[-1] @ X)
         if self.Hblk is not None:
-            # sum_l z^l sum_m B_m h B_{m-l}^T = F(z) h F(1/z)^T with F(w) = sum_m w^m B_m
-            Fz = sum((z ** mm) * self.B[mm] for mm in self.B)
-            Fzi = sum((z ** (-mm)) * self.B[mm] for mm in self.B)
-            Y = Y + Fz @ (self.Hblk @ (Fzi.T @ X))
+            # sum_l z^l sum_m B_m h B_{m-l}^T = F(z) h F(1/z)^T with F(w) = sum_m w^m B_m,
+            # applied term by term: c = sum_m z^{-m} B_m^T X, Y += sum_m z^m B_m (h c)
+            c = sum((z ** (-mm)) * (self.BT[mm] @ X) for mm in self.B)
+            d = self.Hblk @ c
+            Y = Y + sum((z ** mm) * (self.B[mm] @ d) for mm in self.B)
         return Y
 
     def apply_P(self, z, E, X):
@@ -151,11 +154,13 @@ class CellOperator:
         transposes rather than from the identity P(z)^dagger = P(1/conj z) of §3.2, so
         that tests can check that identity."""
         zc = np.conj(z)
-        Y = self.K[0].T @ X + zc * (self.K[1].T @ X) + np.conj(1.0 / z) * (self.K[-1].T @ X)
+        if not hasattr(self, "KT"):
+            self.KT = {b: K.T.tocsr() for b, K in self.K.items()}
+        Y = self.KT[0] @ X + zc * (self.KT[1] @ X) + np.conj(1.0 / z) * (self.KT[-1] @ X)
         if self.Hblk is not None:
-            Fa = sum((np.conj(1.0 / z) ** mm) * self.B[mm] for mm in self.B)
-            Fb = sum((zc ** mm) * self.B[mm] for mm in self.B)
-            Y = Y + Fa @ (self.Hblk.T @ (Fb.T @ X))
+            c = sum((zc ** mm) * (self.BT[mm] @ X) for mm in self.B)
+            d = self.Hblk.T @ c
+            Y = Y + sum((np.conj(1.0 / z) ** mm) * (self.B[mm] @ d) for mm in self.B)
         return np.conj(E) * X - Y
 
     def P_matrix(self, z, E):

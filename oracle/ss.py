@@ -55,18 +55,25 @@ class SSResult:
     S: np.ndarray | None = None
 
 
-def solve_ring(op, E, lambda_min, n_int, V, tol=1e-10, max_iter=20000):
-    """Step 1: primal and dual BiCG at the outer-circle points.  Returns Y1, Y2, iters."""
+def _solve_point(args):
+    op, z, E, V, tol, max_iter = args
+    X, Xt, it, info = bicg(lambda X: op.apply_P(z, E, X), lambda X: op.apply_P_adjoint(z, E, X),
+                           V, V, tol=tol, max_iter=max_iter)
+    return X, Xt, it
+
+
+def solve_ring(op, E, lambda_min, n_int, V, tol=1e-10, max_iter=20000, pool=None):
+    """Step 1: primal and dual BiCG at the outer-circle points.  Returns Y1, Y2, iters.
+    The points are independent (§3.3, middle layer); `pool` (an executor with .map) may
+    solve them in parallel."""
     z1, _, z2, _ = ring_contour(lambda_min, n_int)
     N, L = V.shape
     Y1 = np.zeros((n_int, N, L), complex)
     Y2 = np.zeros((n_int, N, L), complex)
     iters = np.zeros((n_int, L), int)
-    for j in range(n_int):
-        z = z1[j]
-        X, Xt, it, info = bicg(lambda X, z=z: op.apply_P(z, E, X),
-                               lambda X, z=z: op.apply_P_adjoint(z, E, X),
-                               V, V, tol=tol, max_iter=max_iter)
+    jobs = [(op, z1[j], E, V, tol, max_iter) for j in range(n_int)]
+    results = pool.map(_solve_point, jobs) if pool is not None else map(_solve_point, jobs)
+    for j, (X, Xt, it) in enumerate(results):
         Y1[j], Y2[j], iters[j] = X, Xt, it
     return Y1, Y2, iters
 
@@ -145,9 +152,9 @@ def filter_sort(lam, X, res, lambda_min, a, rho_max):
 
 
 def ss_hankel(op, E, lambda_min, n_int, V, M, delta=1e-10, tol=1e-10, rho_max=1e-8,
-              max_iter=20000, keep_moments=False):
+              max_iter=20000, keep_moments=False, pool=None):
     """Whole SS-Hankel pipeline for one energy."""
-    Y1, Y2, iters = solve_ring(op, E, lambda_min, n_int, V, tol=tol, max_iter=max_iter)
+    Y1, Y2, iters = solve_ring(op, E, lambda_min, n_int, V, tol=tol, max_iter=max_iter, pool=pool)
     S, mu = moments(Y1, Y2, lambda_min, n_int, V, M)
     tau, psi, m_hat, sig = hankel_extract(S, mu, M, delta)
     norms = op.frobenius(E)

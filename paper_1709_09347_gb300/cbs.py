@@ -26,7 +26,8 @@ EXPORTS = (
     "cbs_options_default", "cbs_create_hamiltonian", "cbs_hamiltonian_free", "cbs_hamiltonian_size",
     "cbs_hamiltonian_norms", "cbs_apply", "cbs_solve_shifted", "cbs_solve", "cbs_result_count",
     "cbs_result_get", "cbs_result_stats", "cbs_result_all", "cbs_result_moments", "cbs_result_iters",
-    "cbs_result_timing", "cbs_result_free", "cbs_last_error",
+    "cbs_result_timing", "cbs_result_profile", "cbs_result_free", "cbs_last_error",
+    "cbs_kernel_launches",
 )
 
 
@@ -51,7 +52,7 @@ class Options(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("delta", ct.c_double), ("rho_max", ct.c_double),
                 ("max_iter", ct.c_int), ("precision", ct.c_int), ("extraction", ct.c_int),
                 ("check_every", ct.c_int), ("inner_tol", ct.c_double), ("max_sweeps", ct.c_int),
-                ("energies_per_batch", ct.c_int), ("stream", ct.c_void_p)]
+                ("energies_per_batch", ct.c_int), ("profile", ct.c_int), ("stream", ct.c_void_p)]
 
 
 class Stats(ct.Structure):
@@ -97,9 +98,12 @@ def load():
     lib.cbs_result_moments.argtypes = [V, I, P(D)]
     lib.cbs_result_iters.argtypes = [V, I, P(I)]
     lib.cbs_result_timing.argtypes = [V, P(D), P(D), P(D), P(D)]
+    lib.cbs_result_profile.argtypes = [V, I, P(D), P(D), P(D)]
     lib.cbs_result_free.argtypes = [V]
     lib.cbs_result_free.restype = None
     lib.cbs_last_error.restype = ct.c_char_p
+    lib.cbs_kernel_launches.argtypes = []
+    lib.cbs_kernel_launches.restype = ct.c_uint64
     _lib = lib
     return lib
 
@@ -246,6 +250,11 @@ class Result:
         t = [ct.c_double() for _ in range(4)]
         _check(lib.cbs_result_timing(handle, *[ct.byref(x) for x in t]))
         self.ms_solve, self.ms_moments, self.ms_extract, self.ms_total = (x.value for x in t)
+        self.profile = {}
+        for name, dt in (("c128", CBS_C128), ("c64", CBS_C64)):
+            a, b, c = ct.c_double(), ct.c_double(), ct.c_double()
+            _check(lib.cbs_result_profile(handle, dt, ct.byref(a), ct.byref(b), ct.byref(c)))
+            self.profile[name] = dict(ms=a.value, launches=b.value, outputs=c.value)
 
 
 def solve(H: Hamiltonian, energies, lambda_min, n_int, L, M, V, opts: Options | None = None,
@@ -273,3 +282,8 @@ def solve(H: Hamiltonian, energies, lambda_min, n_int, L, M, V, opts: Options | 
     finally:
         if h:
             lib.cbs_result_free(h)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libcbs in this process so far (graph replays count every node)."""
+    return int(load().cbs_kernel_launches())

@@ -2,6 +2,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 
 #include "kernels.cuh"
@@ -9,6 +10,11 @@
 namespace cbs {
 
 static thread_local std::string g_err;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_err = msg; }
 
@@ -22,6 +28,8 @@ cbs_status cuda_fail(cudaError_t e, const char *what) {
 using namespace cbs;
 
 extern "C" const char *cbs_last_error(void) { return g_err.c_str(); }
+
+extern "C" uint64_t cbs_kernel_launches(void) { return launches_so_far(); }
 
 extern "C" cbs_status cbs_options_default(cbs_options *o) {
   if (!o) return CBS_EINVAL;

@@ -12,7 +12,8 @@
 // scatter-as-gather through the transposed table inside the stencil kernel.
 //
 // Layout: X, Y are [n_sys][N][L] (columns of a grid point contiguous).  Thread blocks are
-// (L, PY): threadIdx.x is the column, threadIdx.y a lane over grid points.
+// (L, PY): threadIdx.x is the column; threadIdx.y a lane over support entries (gather)
+// or over x (stencil, one block per (x-chunk, y, system), marching along z).
 #include "common.cuh"
 
 namespace cbs {
@@ -82,103 +83,100 @@ __global__ void k_proj_gather(HamView H, int L, const typename CT<R>::T *__restr
   }
 }
 
-__device__ __forceinline__ int wrap_plus(int i, int k, int n) {
-  int j = i + k;
-  if (j >= n) j -= n;
-  if (j >= n) j %= n;
-  return j;
-}
-__device__ __forceinline__ int wrap_minus(int i, int k, int n) {
-  int j = i - k;
-  if (j < 0) j += n;
-  if (j < 0) j = ((j % n) + n) % n;
+__device__ __forceinline__ int wrap_idx(int j, int n) {
+  // j in (-n*kMaxHalf, n*(kMaxHalf+1)): fold into [0, n)
+  while (j >= n) j -= n;
+  while (j < 0) j += n;
   return j;
 }
 
-constexpr int kApplyPPT = 4;  // grid points per thread
-
-template <typename R, bool PER_COL>
-__global__ void k_apply(HamView H, int L, const typename CT<R>::T *__restrict__ X,
-                        typename CT<R>::T *__restrict__ Y, const double2 *__restrict__ twist,
-                        const double *__restrict__ E, const typename CT<R>::T *__restrict__ D,
-                        const int *__restrict__ sys_active) {
+// z-marching stencil: a thread owns one column c of one (x, y) grid line and walks the
+// planes iz = 0..nz-1, keeping the 2*MH+1 planes around iz in registers.  The register
+// queue holds the Bloch-extended field psi(p) = w^{floor(p/nz)} X[p mod nz] (Eq. (3)), so
+// the twist of arms that cross the cell faces along z is applied once when a plane
+// enters the queue.  x and y arms are plain periodic and read through L1/L2 with
+// neighbour offsets precomputed once per thread.  Indices inside one system are 32-bit.
+template <typename R, bool PER_COL, int MH>
+__global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typename CT<R>::T *__restrict__ X,
+                                                  typename CT<R>::T *__restrict__ Y,
+                                                  const double2 *__restrict__ twist,
+                                                  const double *__restrict__ E,
+                                                  const typename CT<R>::T *__restrict__ D,
+                                                  const int *__restrict__ sys_active) {
   typedef typename CT<R>::T C;
-  const int s = blockIdx.y;
+  const int s = blockIdx.z;
   if (sys_active && !sys_active[s]) return;
-  const int c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
+  const int c = threadIdx.x;
+  const int ix = blockIdx.x * blockDim.y + threadIdx.y;
+  const int iy = blockIdx.y;
+  if (ix >= H.nx) return;
+  const int nx = H.nx, ny = H.ny, nz = H.nz;
+  const int nxy = nx * ny;
   double2 wd = twist[PER_COL ? (int64_t)s * L + c : s];
   double2 wid = cdiv(make_double2(1.0, 0.0), wd);
   const C w = from_d<R>(wd), wi = from_d<R>(wid);
   const R e = (R)E[s];
   const R dk = (R)H.diag_kin;
-  R wx[kMaxHalf + 1], wy[kMaxHalf + 1], wz[kMaxHalf + 1];
+  R wx[MH + 1], wy[MH + 1], wz[MH + 1];
+  int ox_p[MH + 1], ox_m[MH + 1], oy_p[MH + 1], oy_m[MH + 1];
 #pragma unroll
-  for (int k = 1; k <= kMaxHalf; ++k) { wx[k] = (R)H.wx[k]; wy[k] = (R)H.wy[k]; wz[k] = (R)H.wz[k]; }
+  for (int k = 1; k <= MH; ++k) {
+    wx[k] = (R)H.wx[k]; wy[k] = (R)H.wy[k]; wz[k] = (R)H.wz[k];
+    ox_p[k] = (wrap_idx(ix + k, nx) - ix) * L;
+    ox_m[k] = (wrap_idx(ix - k, nx) - ix) * L;
+    oy_p[k] = (wrap_idx(iy + k, ny) - iy) * nx * L;
+    oy_m[k] = (wrap_idx(iy - k, ny) - iy) * nx * L;
+  }
   const R *vl = vloc_ptr<R>(H);
   const R *pv = pval_ptr<R>(H);
   const int np = H.n_proj;
-  const int64_t nxy = (int64_t)H.nx * H.ny;
   const C *Xs = X + (int64_t)s * H.n * L;
   C *Ys = Y + (int64_t)s * H.n * L;
-  const int64_t base = (int64_t)blockIdx.x * py * kApplyPPT;
-  for (int k0 = 0; k0 < kApplyPPT; ++k0) {
-    const int64_t i = base + (int64_t)k0 * py + ly;
-    if (i >= H.n) break;
-    const int ix = (int)(i % H.nx);
-    const int iy = (int)((i / H.nx) % H.ny);
-    const int iz = (int)(i / nxy);
-    const C x0 = Xs[i * L + c];
-    const R d = dk + vl[i];
-    C acc = mk<R>(d * x0.x, d * x0.y);
-    C top = mk<R>(0, 0), bot = mk<R>(0, 0);
-    const int64_t rowx = i - ix, rowy = i - (int64_t)iy * H.nx;
+  const int line = iy * nx + ix;           // (x, y) offset inside a plane
+  // psi(p) for p in [-nz, 2 nz)
+  auto bloch = [&](int p) -> C {
+    if (p >= nz) return cmul(w, Xs[((p - nz) * nxy + line) * L + c]);
+    if (p < 0) return cmul(wi, Xs[((p + nz) * nxy + line) * L + c]);
+    return Xs[(p * nxy + line) * L + c];
+  };
+  C q[2 * MH + 1];
 #pragma unroll
-    for (int k = 1; k <= kMaxHalf; ++k) {
-      if (k > H.m) break;
-      C a1 = Xs[(rowx + wrap_plus(ix, k, H.nx)) * L + c];
-      C a2 = Xs[(rowx + wrap_minus(ix, k, H.nx)) * L + c];
-      acc.x += wx[k] * (a1.x + a2.x);
-      acc.y += wx[k] * (a1.y + a2.y);
-      C b1 = Xs[(rowy + (int64_t)wrap_plus(iy, k, H.ny) * H.nx) * L + c];
-      C b2 = Xs[(rowy + (int64_t)wrap_minus(iy, k, H.ny) * H.nx) * L + c];
-      acc.x += wy[k] * (b1.x + b2.x);
-      acc.y += wy[k] * (b1.y + b2.y);
-      int zu = iz + k, zd = iz - k;
-      if (zu < H.nz) {
-        C u = Xs[(i + k * nxy) * L + c];
-        acc.x += wz[k] * u.x; acc.y += wz[k] * u.y;
-      } else {
-        C u = Xs[(i + (int64_t)(k - H.nz) * nxy) * L + c];
-        top.x += wz[k] * u.x; top.y += wz[k] * u.y;
-      }
-      if (zd >= 0) {
-        C u = Xs[(i - k * nxy) * L + c];
-        acc.x += wz[k] * u.x; acc.y += wz[k] * u.y;
-      } else {
-        C u = Xs[(i + (int64_t)(H.nz - k) * nxy) * L + c];
-        bot.x += wz[k] * u.x; bot.y += wz[k] * u.y;
-      }
+  for (int d = 0; d < 2 * MH; ++d) q[d] = bloch(d - MH);
+  for (int iz = 0; iz < nz; ++iz) {
+    q[2 * MH] = bloch(iz + MH);
+    const int pt = iz * nxy + line;
+    const int b = pt * L + c;
+    const C x0 = q[MH];
+    const R dd = dk + vl[pt];
+    C acc = mk<R>(dd * x0.x, dd * x0.y);
+#pragma unroll
+    for (int k = 1; k <= MH; ++k) {
+      const C a1 = Xs[b + ox_p[k]], a2 = Xs[b + ox_m[k]];
+      const C b1 = Xs[b + oy_p[k]], b2 = Xs[b + oy_m[k]];
+      const C z1 = q[MH + k], z2 = q[MH - k];
+      acc.x += wx[k] * (a1.x + a2.x) + wy[k] * (b1.x + b2.x) + wz[k] * (z1.x + z2.x);
+      acc.y += wx[k] * (a1.y + a2.y) + wy[k] * (b1.y + b2.y) + wz[k] * (z1.y + z2.y);
     }
-    acc = cfma(w, top, acc);
-    acc = cfma(wi, bot, acc);
     if (D) {
-      const int64_t e0 = H.pt_ptr[i], e1 = H.pt_ptr[i + 1];
-      for (int64_t q = e0; q < e1; ++q) {
-        const int t = H.pt_ent[q], a = H.pt_atom[q];
+      const int e0 = (int)H.pt_ptr[pt], e1 = (int)H.pt_ptr[pt + 1];
+      for (int qq = e0; qq < e1; ++qq) {
+        const int t = H.pt_ent[qq], a = H.pt_atom[qq];
         const C *Da = D + (((int64_t)s * H.n_atoms + a) * np) * L + c;
         C v = mk<R>(0, 0);
         for (int mu = 0; mu < np; ++mu) {
-          R p = pv[(int64_t)t * np + mu];
-          C dv = Da[(int64_t)mu * L];
+          const R p = pv[t * np + mu];
+          const C dv = Da[mu * L];
           v.x += p * dv.x;
           v.y += p * dv.y;
         }
-        int m = H.sup_wrap[t];
+        const int m = H.sup_wrap[t];
         if (m == 0) acc = cadd(acc, v);
         else acc = cfma(m > 0 ? w : wi, v, acc);                      // w^{m} v
       }
     }
-    Ys[i * L + c] = mk<R>(e * x0.x - acc.x, e * x0.y - acc.y);
+    Ys[b] = mk<R>(e * x0.x - acc.x, e * x0.y - acc.y);
+#pragma unroll
+    for (int d = 0; d < 2 * MH; ++d) q[d] = q[d + 1];
   }
 }
 
@@ -198,6 +196,7 @@ cbs_status launch_proj_gather(const HamView &H, int n_sys, int L, const typename
     k_proj_gather<R, true><<<grd, blk, sm, st>>>(H, L, X, twist, D, sys_active);
   else
     k_proj_gather<R, false><<<grd, blk, sm, st>>>(H, L, X, twist, D, sys_active);
+  cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -207,13 +206,29 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
                         typename CT<R>::T *Y, const double2 *twist, bool per_col,
                         const double *E, const typename CT<R>::T *D, const int *sys_active,
                         cudaStream_t st) {
+  if ((int64_t)H.n * L >= ((int64_t)1 << 31)) {
+    set_error("apply: N*L must be below 2^31");
+    return CBS_EINVAL;
+  }
   dim3 blk = col_block(L);
-  dim3 grd((unsigned)ceil_div(H.n, (int64_t)blk.y * kApplyPPT), (unsigned)n_sys, 1);
+  dim3 grd((unsigned)ceil_div(H.nx, blk.y), (unsigned)H.ny, (unsigned)n_sys);
   const typename CT<R>::T *Dp = H.n_atoms ? D : nullptr;
-  if (per_col)
-    k_apply<R, true><<<grd, blk, 0, st>>>(H, L, X, Y, twist, E, Dp, sys_active);
-  else
-    k_apply<R, false><<<grd, blk, 0, st>>>(H, L, X, Y, twist, E, Dp, sys_active);
+#define ZM(MH)                                                                                  \
+  do {                                                                                          \
+    if (per_col) k_apply_zm<R, true, MH><<<grd, blk, 0, st>>>(H, L, X, Y, twist, E, Dp, sys_active); \
+    else k_apply_zm<R, false, MH><<<grd, blk, 0, st>>>(H, L, X, Y, twist, E, Dp, sys_active);   \
+    cbs::count_launches(1);                                                                     \
+  } while (0)
+  switch (H.m) {
+    case 1: ZM(1); break;
+    case 2: ZM(2); break;
+    case 3: ZM(3); break;
+    case 4: ZM(4); break;
+    case 5: ZM(5); break;
+    case 6: ZM(6); break;
+    default: set_error("apply: FD half-width must be 1..6"); return CBS_EINVAL;
+  }
+#undef ZM
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }

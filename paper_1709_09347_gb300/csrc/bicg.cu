@@ -127,9 +127,11 @@ __global__ void k_dot_pq(int n, int64_t N, int L, int chunk_pts, int n_chunks,
 }
 
 __global__ void k_reduce_alpha(int n, int L, int n_chunks, const double *part, const double2 *rho,
-                               double2 *alpha, int *active, int *flags, const int *sys_active) {
+                               double2 *alpha, int *active, int *flags, const int *sys_active,
+                               unsigned long long *sys_apply) {
   const int s = blockIdx.x, c = threadIdx.x;
   if (!sys_active[s]) return;
+  if (c == 0 && sys_apply) atomicAdd(sys_apply, 1ull);   // system s went through this apply
   const int64_t k = (int64_t)s * L + c;
   if (!active[k]) { alpha[k] = make_double2(0, 0); return; }
   double gx = 0, gy = 0;
@@ -234,7 +236,7 @@ __global__ void k_twists(int n, const double2 *z, const double *E, double2 *tw, 
 
 cbs_status launch_twists(int n, const double2 *z, const double *E, double2 *tw, double *E2,
                          cudaStream_t st) {
-  k_twists<<<ceil_div(n, 128), 128, 0, st>>>(n, z, E, tw, E2);
+  k_twists<<<ceil_div(n, 128), 128, 0, st>>>(n, z, E, tw, E2); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -262,7 +264,7 @@ size_t Bicg<R>::bytes_needed(const HamView &H, int n, int L) {
   b += align256((int64_t)2 * n * sizeof(double2)) + align256((int64_t)2 * n * sizeof(double));
   b += 3 * align256((int64_t)n * L * sizeof(double2)) + 2 * align256((int64_t)n * L * sizeof(double));
   b += 3 * align256((int64_t)n * L * sizeof(int)) + align256((int64_t)2 * n * sizeof(int)) + 256;
-  b += align256((int64_t)n * nc * L * 4 * sizeof(double));
+  b += align256((int64_t)n * nc * L * 4 * sizeof(double)) + 256;
   return (size_t)b;
 }
 
@@ -295,6 +297,8 @@ cbs_status Bicg<R>::alloc(const HamView &H_, int n_, int L_) {
   sys_active = (int *)take((int64_t)2 * n * sizeof(int));
   n_active = (int *)take(256);
   part = (double *)take((int64_t)n * n_chunks * L * 4 * sizeof(double));
+  sys_apply = (unsigned long long *)take(256);
+  CBS_CUDA(cudaMemset(sys_apply, 0, sizeof(unsigned long long)));
   return CBS_OK;
 }
 
@@ -302,6 +306,17 @@ template <typename R>
 void Bicg<R>::release() {
   if (block) cudaFree(block);
   block = nullptr;
+  for (int k = 0; k < n_prof_ev; ++k) cudaEventDestroy(prof_ev[k]);
+  n_prof_ev = 0;
+}
+
+template <typename R>
+cbs_status Bicg<R>::prof_outputs(cudaStream_t st, double *out) {
+  unsigned long long v = 0;
+  CBS_CUDA(cudaMemcpyAsync(&v, sys_apply, sizeof(v), cudaMemcpyDeviceToHost, st));
+  CBS_CUDA(cudaStreamSynchronize(st));
+  *out = 2.0 * (double)v * (double)N * (double)L;
+  return CBS_OK;
 }
 
 template <typename R>
@@ -320,33 +335,37 @@ cbs_status Bicg<R>::init(const double2 *B, int64_t bstride, const double2 *Bd, i
   dim3 blk = col_block(L);
   dim3 grd((unsigned)n_chunks, (unsigned)n, 1);
   k_init<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, B, bstride, Bd, bdstride,
-                                          x, r, p, part);
+                                          x, r, p, part); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   CBS_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
   k_reduce_init<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, beta, nb, nbd, active, iters, flags,
-                                 colmask, sys_active, n_active);
+                                 colmask, sys_active, n_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
 
 template <typename R>
-cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st) {
+cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st, int kk) {
   dim3 blk = col_block(L);
   dim3 grd((unsigned)n_chunks, (unsigned)n, 1);
-  k_update_p<R><<<grd, blk, 0, st>>>(n, N, L, chunk_pts, r, p, beta, active, sys_active);
+  k_update_p<R><<<grd, blk, 0, st>>>(n, N, L, chunk_pts, r, p, beta, active, sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
+  const bool prof = profile && kk >= 0 && 2 * kk + 1 < n_prof_ev;
+  if (prof) CBS_CUDA(cudaEventRecord(prof_ev[2 * kk], st));
   cbs_status s = apply_P<R>(H, 2 * n, L, p, q, tw, false, E, D, sys_active, st);
   if (s != CBS_OK) return s;
-  k_dot_pq<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, p, q, part, sys_active);
+  if (prof) CBS_CUDA(cudaEventRecord(prof_ev[2 * kk + 1], st));
+  k_dot_pq<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, p, q, part, sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
-  k_reduce_alpha<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, alpha, active, flags, sys_active);
+  k_reduce_alpha<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, alpha, active, flags, sys_active,
+                                  sys_apply); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   k_pass_b<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, x, r, p, q, alpha,
-                                             active, part, sys_active);
+                                             active, part, sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   CBS_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
   k_reduce_beta<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, beta, nb, nbd, active, iters, flags,
-                                 tol, max_iter, sys_active, n_active);
+                                 tol, max_iter, sys_active, n_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -355,12 +374,20 @@ template <typename R>
 cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStream_t st,
                             int *host_iters_done) {
   if (check_every < 1) check_every = 1;
+  if (profile && n_prof_ev == 0) {
+    const int ne = 2 * (check_every < 64 ? check_every : 64);
+    for (int k = 0; k < ne; ++k) CBS_CUDA(cudaEventCreate(&prof_ev[k]));
+    n_prof_ev = ne;
+  }
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  const uint64_t c0 = launches_so_far();
   CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cbs_status s = CBS_OK;
-  for (int k = 0; k < check_every && s == CBS_OK; ++k) s = step(tol, max_iter, st);
+  for (int k = 0; k < check_every && s == CBS_OK; ++k) s = step(tol, max_iter, st, k);
   cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  const uint64_t per_graph = launches_so_far() - c0;
+  uncount_launches(per_graph);
   if (s != CBS_OK) { if (graph) cudaGraphDestroy(graph); return s; }
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
   ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -376,9 +403,19 @@ cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStrea
   const int max_replays = max_iter / check_every + 2;
   for (int rep = 0; rep < max_replays; ++rep) {
     ce = cudaGraphLaunch(exec, st);
+    count_launches(per_graph);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { s = cuda_fail(ce, "BiCG graph replay"); break; }
+    if (profile) {
+      for (int k = 0; 2 * k + 1 < n_prof_ev && k < check_every; ++k) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, prof_ev[2 * k], prof_ev[2 * k + 1]) == cudaSuccess) {
+          prof_ms += ms;
+          prof_launches += 1;
+        }
+      }
+    }
     done += check_every;
     if (*h_active == 0) break;
   }
@@ -425,7 +462,7 @@ cbs_status launch_residual(int n2, int64_t N, int L, const double2 *B, int64_t b
   dim3 blk = col_block(L);
   dim3 grd(64, (unsigned)n2, 1);
   k_residual<<<grd, blk, (size_t)blk.x * blk.y * sizeof(double), st>>>(n, N, L, B, bstride, Bd,
-                                                                        bdstride, AY, colnorm2);
+                                                                        bdstride, AY, colnorm2); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -440,7 +477,7 @@ __global__ void k_accumulate(int64_t count, double2 *Y, const float2 *X) {
 }
 
 cbs_status launch_accumulate(int64_t count, double2 *Y, const float2 *X, cudaStream_t st) {
-  k_accumulate<<<152 * 8, 256, 0, st>>>(count, Y, X);
+  k_accumulate<<<152 * 8, 256, 0, st>>>(count, Y, X); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -470,7 +507,7 @@ __global__ void k_refine_check(int n, int L, int nchunks, const double *colnorm2
 cbs_status launch_refine_check(int n, int L, int nchunks, const double *colnorm2, const double *bnorm,
                                double tol, int *colmask, int *n_unconv, double *maxrel,
                                cudaStream_t st) {
-  k_refine_check<<<n, L, 0, st>>>(n, L, nchunks, colnorm2, bnorm, tol, colmask, n_unconv, maxrel);
+  k_refine_check<<<n, L, 0, st>>>(n, L, nchunks, colnorm2, bnorm, tol, colmask, n_unconv, maxrel); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }

@@ -25,6 +25,12 @@ struct Bicg {
   double *part = nullptr;                                     // [n][n_chunks][L][4]
   void *block = nullptr;
   size_t bytes = 0;
+  // profiling of the operator-apply launches (events around each apply inside the graph)
+  bool profile = false;
+  cudaEvent_t prof_ev[2 * 64] = {};
+  int n_prof_ev = 0;
+  unsigned long long *sys_apply = nullptr;   // device: active systems summed over applies
+  double prof_ms = 0, prof_launches = 0;
 
   static size_t bytes_needed(const HamView &H, int n, int L);
   cbs_status alloc(const HamView &H, int n, int L);
@@ -38,8 +44,10 @@ struct Bicg {
   // Iterate until every column converged, broke down or reached max_iter.
   cbs_status iterate(double tol, int max_iter, int check_every, cudaStream_t st,
                      int *host_iters_done);
-  // one iteration (captured into graphs)
-  cbs_status step(double tol, int max_iter, cudaStream_t st);
+  // one iteration (captured into graphs); k indexes the iteration inside the graph
+  cbs_status step(double tol, int max_iter, cudaStream_t st, int k);
+  // outputs written by the apply launches so far (2 * active systems * N * L)
+  cbs_status prof_outputs(cudaStream_t st, double *out);
 };
 
 // Elementwise helpers used by the refinement driver.

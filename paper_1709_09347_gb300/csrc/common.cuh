@@ -118,6 +118,11 @@ namespace cbs {
 void set_error(const std::string &msg);
 cbs_status cuda_fail(cudaError_t e, const char *what);
 
+// kernel-launch accounting (cbs_kernel_launches)
+void count_launches(uint64_t n);
+void uncount_launches(uint64_t n);   // kernels recorded into a graph, not run
+uint64_t launches_so_far();
+
 #define CBS_CUDA(call)                                   \
   do {                                                   \
     cudaError_t _e = (call);                             \

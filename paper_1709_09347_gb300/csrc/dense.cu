@@ -248,6 +248,7 @@ cbs_status zgemm(int opa, int opb, int M, int N, int K, double2 alpha, const dou
   else if (opa == 1 && opb == 1) ZG(1, 1);
   else { set_error("zgemm: unsupported op pair"); return CBS_EINVAL; }
 #undef ZG
+  cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -585,7 +586,7 @@ __global__ void k_gather_vectors(int64_t N, int cnt, int nk, const double2 *Psi,
 cbs_status launch_hankel(int n_e, int L, int M, const double2 *mu, double2 *T, double2 *Tl,
                          cudaStream_t st) {
   const int64_t nn = (int64_t)L * M * L * M;
-  k_hankel<<<dim3((unsigned)ceil_div(nn, 256), (unsigned)n_e, 1), 256, 0, st>>>(n_e, L, M, mu, T, Tl);
+  k_hankel<<<dim3((unsigned)ceil_div(nn, 256), (unsigned)n_e, 1), 256, 0, st>>>(n_e, L, M, mu, T, Tl); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -593,20 +594,20 @@ cbs_status launch_hankel(int n_e, int L, int M, const double2 *mu, double2 *T, d
 cbs_status launch_svd(int n_e, int n, double2 *A, double2 *W, double2 *U, double2 *Ws,
                       double *sig, int *info, cudaStream_t st) {
   if (n > 512) { set_error("L*M must be <= 512"); return CBS_EINVAL; }
-  k_svd<<<n_e, kSvdThreads, 0, st>>>(n, A, W, U, Ws, sig, info, 1e-14, 60);
+  k_svd<<<n_e, kSvdThreads, 0, st>>>(n, A, W, U, Ws, sig, info, 1e-14, 60); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
 
 cbs_status launch_rank(int n_e, int n, const double *sig, double delta, int *mhat, cudaStream_t st) {
-  k_rank<<<ceil_div(n_e, 64), 64, 0, st>>>(n_e, n, sig, delta, mhat);
+  k_rank<<<ceil_div(n_e, 64), 64, 0, st>>>(n_e, n, sig, delta, mhat); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
 
 cbs_status launch_scale(int n_e, int rows, int ld, const int *mhat, const double *sig, double2 *B,
                         int rows_scale, cudaStream_t st) {
-  k_scale_cols<<<dim3(64, (unsigned)n_e, 1), 256, 0, st>>>(rows, ld, mhat, sig, B, rows_scale);
+  k_scale_cols<<<dim3(64, (unsigned)n_e, 1), 256, 0, st>>>(rows, ld, mhat, sig, B, rows_scale); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -615,7 +616,7 @@ cbs_status launch_eig(int n_e, int ld, const int *mhat, double2 *B, double2 *Z, 
                       double2 *Yc, int *nring, int *ringidx, double lambda_min, int *info,
                       cudaStream_t st) {
   if (ld > 512) { set_error("L*M must be <= 512"); return CBS_EINVAL; }
-  k_eig<<<n_e, kEigThreads, 0, st>>>(ld, mhat, B, Z, tau, Yc, nring, ringidx, lambda_min, info);
+  k_eig<<<n_e, kEigThreads, 0, st>>>(ld, mhat, B, Z, tau, Yc, nring, ringidx, lambda_min, info); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -627,10 +628,10 @@ cbs_status launch_filter(int64_t N, int cnt, const double2 *tau_ring, const doub
                          cudaStream_t st) {
   if (cnt <= 0) return CBS_OK;
   if (cnt > 512) { set_error("too many in-ring eigenvalues"); return CBS_EINVAL; }
-  k_colstats<<<cnt, 256, 0, st>>>(N, cnt, Psi, Res, stats);
+  k_colstats<<<cnt, 256, 0, st>>>(N, cnt, Psi, Res, stats); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   k_filter<<<1, 512, 0, st>>>(cnt, tau_ring, stats, nHp, nA, nHm, rho_max, a_cell, Psi, N, rho_all,
-                              n_keep, perm, lam_out, k_out, rho_out, scale_out);
+                              n_keep, perm, lam_out, k_out, rho_out, scale_out); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -638,7 +639,7 @@ cbs_status launch_filter(int64_t N, int cnt, const double2 *tau_ring, const doub
 cbs_status launch_gather_vectors(int64_t N, int cnt, int nk, const double2 *Psi, const int *perm,
                                  const double2 *scale, double2 *Out, cudaStream_t st) {
   if (nk <= 0) return CBS_OK;
-  k_gather_vectors<<<152 * 4, 256, 0, st>>>(N, cnt, nk, Psi, perm, scale, Out);
+  k_gather_vectors<<<152 * 4, 256, 0, st>>>(N, cnt, nk, Psi, perm, scale, Out); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }

@@ -310,8 +310,8 @@ static cbs_status create_impl(const cbs_grid *g, const double *v_loc, const cbs_
   CBS_CUDA(cudaMalloc(&out, 5 * sizeof(double) + sizeof(int)));
   err = (int *)(out + 5);
   CBS_CUDA(cudaMemset(err, 0, sizeof(int)));
-  k_frobenius<<<nb, threads>>>(v, part, err);
-  k_sum_parts<<<1, 32>>>(part, nb, out);
+  k_frobenius<<<nb, threads>>>(v, part, err); cbs::count_launches(1);
+  k_sum_parts<<<1, 32>>>(part, nb, out); cbs::count_launches(1);
   double res[5];
   int herr = 0;
   cudaError_t e1 = cudaMemcpy(res, out, sizeof(res), cudaMemcpyDeviceToHost);

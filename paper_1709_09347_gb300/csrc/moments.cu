@@ -34,7 +34,7 @@ __global__ void k_contour(int n_int, int M2, double lambda_min, double2 *coef, d
 
 cbs_status launch_contour(int n_int, int M, double lambda_min, double2 *coef, double2 *z1,
                           cudaStream_t st) {
-  k_contour<<<n_int, 64, 0, st>>>(n_int, 2 * M, lambda_min, coef, z1);
+  k_contour<<<n_int, 64, 0, st>>>(n_int, 2 * M, lambda_min, coef, z1); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -84,6 +84,7 @@ cbs_status launch_moments(int n, int n_e, int n_int, int M, int64_t N, int L, co
     set_error("M must be <= 16");
     return CBS_EINVAL;
   }
+  cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -172,9 +173,10 @@ cbs_status launch_mu(int n, int n_e, int n_int, int M, int64_t N, int L, const d
   if (L * L <= 4 * 256) k_vhy<4><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
   else if (L * L <= 9 * 256) k_vhy<9><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
   else k_vhy<16><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
+  cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   k_mu<<<dim3((unsigned)(2 * M), (unsigned)n_e, 1), 256, 0, st>>>(n, n_int, 2 * M, L, nch, part,
-                                                                 coef, mu);
+                                                                 coef, mu); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }

@@ -24,6 +24,7 @@ struct cbs_result {
   int64_t N = 0;
   std::vector<cbs_energy_result> e;
   double ms_solve = 0, ms_moments = 0, ms_extract = 0, ms_total = 0;
+  double prof_ms[2] = {0, 0}, prof_launches[2] = {0, 0}, prof_outputs[2] = {0, 0};
 };
 
 namespace cbs {
@@ -132,12 +133,31 @@ struct ResidualCheck {
     return CBS_OK;
   }
   // Y: [2n][N][L]; tw/E: twists [2n] and energies [2n]
+  bool profile = false;
+  double prof_ms = 0, prof_launches = 0, prof_outputs = 0;
   cbs_status run(const HamView &H, const double2 *Y, const double2 *B, const double2 *tw,
                  const double *E, double tol, cudaStream_t st, int *host_unconv) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (profile) {
+      CBS_CUDA(cudaEventCreate(&e0));
+      CBS_CUDA(cudaEventCreate(&e1));
+      CBS_CUDA(cudaEventRecord(e0, st));
+    }
     CBS_TRY(apply_P<double>(H, 2 * n, L, Y, R, tw, false, E, D, nullptr, st));
+    if (profile) {
+      CBS_CUDA(cudaEventRecord(e1, st));
+      CBS_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      CBS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      prof_ms += ms;
+      prof_launches += 1;
+      prof_outputs += 2.0 * n * (double)N * L;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
     CBS_TRY(launch_residual(2 * n, N, L, B, 0, B, 0, n, R, cn, st));
-    k_col_norms<<<1, L, 0, st>>>(N, L, B, bn);
-    k_bnorm_expand<<<2 * n, L, 0, st>>>(2 * n, L, bn, bn2);
+    k_col_norms<<<1, L, 0, st>>>(N, L, B, bn); cbs::count_launches(1);
+    k_bnorm_expand<<<2 * n, L, 0, st>>>(2 * n, L, bn, bn2); cbs::count_launches(1);
     CBS_CUDA(cudaGetLastError());
     CBS_CUDA(cudaMemsetAsync(nunc, 0, sizeof(int), st));
     CBS_TRY(launch_refine_check(n, L, 64, cn, bn2, tol, colmask, nunc, maxrel, st));
@@ -162,6 +182,19 @@ struct ShiftedSolver {
   std::vector<int> iters, flags;
   std::vector<double> maxrel;
   int sweeps = 0;
+  double prof_ms[2] = {0, 0}, prof_launches[2] = {0, 0}, prof_outputs[2] = {0, 0};
+  cbs_status collect_profile(cudaStream_t st) {
+    double o64 = 0, o32 = 0;
+    if (b64.block && b64.profile) CBS_TRY(b64.prof_outputs(st, &o64));
+    if (b32.block && b32.profile) CBS_TRY(b32.prof_outputs(st, &o32));
+    prof_ms[CBS_C128] = b64.prof_ms + rc.prof_ms;
+    prof_launches[CBS_C128] = b64.prof_launches + rc.prof_launches;
+    prof_outputs[CBS_C128] = o64 + rc.prof_outputs;
+    prof_ms[CBS_C64] = b32.prof_ms;
+    prof_launches[CBS_C64] = b32.prof_launches;
+    prof_outputs[CBS_C64] = o32;
+    return CBS_OK;
+  }
 
   ~ShiftedSolver() { b64.release(); b32.release(); }
 
@@ -178,6 +211,8 @@ struct ShiftedSolver {
     flags.assign((size_t)n * L, 0);
     maxrel.assign((size_t)n * L, 0.0);
     CBS_TRY(rc.alloc(H, n, L));
+    rc.profile = o.profile != 0;
+    b64.profile = b32.profile = o.profile != 0;
     std::vector<int> it_tmp((size_t)n * L), fl_tmp((size_t)n * L);
     if (o.precision == CBS_FP64) {
       CBS_TRY(b64.alloc(H, n, L));
@@ -192,7 +227,7 @@ struct ShiftedSolver {
       CBS_CUDA(cudaMemcpyAsync(maxrel.data(), rc.maxrel, (size_t)n * L * sizeof(double), cudaMemcpyDeviceToHost, st));
       CBS_CUDA(cudaStreamSynchronize(st));
       sweeps = 0;
-      return CBS_OK;
+      return collect_profile(st);
     }
     // complex64 BiCG inside FP64 iterative refinement:
     //   R = B - P(z) Y, R~ = B - P(z)^dagger Y~  (FP64)
@@ -229,7 +264,7 @@ struct ShiftedSolver {
     CBS_CUDA(cudaStreamSynchronize(st));
     for (size_t k = 0; k < mask.size(); ++k)
       if (mask[k]) flags[k] |= 1;
-    return CBS_OK;
+    return collect_profile(st);
   }
 };
 
@@ -338,11 +373,16 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
     CBS_TRY(sysb.alloc((size_t)nsys * (sizeof(double2) + sizeof(double)) + 256));
     double2 *zs = sysb.as<double2>();
     double *Es = (double *)(zs + nsys);
-    k_expand_systems<<<ceil_div(nsys, 128), 128, 0, st>>>(ne, n_int, z1, dE + e0, zs, Es);
+    k_expand_systems<<<ceil_div(nsys, 128), 128, 0, st>>>(ne, n_int, z1, dE + e0, zs, Es); cbs::count_launches(1);
     CBS_CUDA(cudaGetLastError());
     // ---- step 1: shifted solves
     ShiftedSolver S;
     CBS_TRY(S.run(H, nsys, L, zs, Es, dV, o, st));
+    for (int t = 0; t < 2; ++t) {
+      res->prof_ms[t] += S.prof_ms[t];
+      res->prof_launches[t] += S.prof_launches[t];
+      res->prof_outputs[t] += S.prof_outputs[t];
+    }
     CBS_TRY(lap(&res->ms_solve));
     // ---- step 2: moments
     DevBuf mbuf;
@@ -450,12 +490,12 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
       double *Ed = (double *)take(256);
       CBS_CUDA(cudaMemcpyAsync(Ed, &Ee, sizeof(double), cudaMemcpyHostToDevice, st));
       CBS_TRY(zgemm(0, 0, m, cnt, m, one, Z + nn * e, n, 0, Yc + nn * e, n, 0, zero, P1, n, 0, 1, st));
-      k_scale_rows<<<64, 256, 0, st>>>(m, cnt, n, sig + (size_t)e * n, P1);
+      k_scale_rows<<<64, 256, 0, st>>>(m, cnt, n, sig + (size_t)e * n, P1); cbs::count_launches(1);
       CBS_CUDA(cudaGetLastError());
       CBS_TRY(zgemm(0, 0, n, cnt, m, one, Ws + nn * e, n, 0, P1, n, 0, zero, C2, n, 0, 1, st));
       // Psi (row-major N x cnt) = S (row-major N x n) C2  <=>  Psi^T = C2^T S^T (column-major)
       CBS_TRY(zgemm(1, 0, cnt, (int)N, n, one, C2, n, 0, Sm + (size_t)e * N * n, n, 0, zero, Psi, cnt, 0, 1, st));
-      k_gather_tau<<<ceil_div(cnt, 128), 128, 0, st>>>(cnt, tau + (size_t)e * n, ridx + (size_t)e * n, twr);
+      k_gather_tau<<<ceil_div(cnt, 128), 128, 0, st>>>(cnt, tau + (size_t)e * n, ridx + (size_t)e * n, twr); cbs::count_launches(1);
       CBS_CUDA(cudaGetLastError());
       CBS_TRY(apply_P<double>(H, 1, cnt, Psi, Res, twr, true, Ed, Dd, nullptr, st));
       double nHp, nA, nHm;
@@ -575,6 +615,15 @@ extern "C" cbs_status cbs_result_timing(const cbs_result *r, double *ms_solve, d
   if (ms_moments) *ms_moments = r->ms_moments;
   if (ms_extract) *ms_extract = r->ms_extract;
   if (ms_total) *ms_total = r->ms_total;
+  return CBS_OK;
+}
+
+extern "C" cbs_status cbs_result_profile(const cbs_result *r, int dtype, double *ms, double *launches,
+                                         double *outputs) {
+  if (!r || (dtype != CBS_C128 && dtype != CBS_C64)) { set_error("bad result or dtype"); return CBS_EINVAL; }
+  if (ms) *ms = r->prof_ms[dtype];
+  if (launches) *launches = r->prof_launches[dtype];
+  if (outputs) *outputs = r->prof_outputs[dtype];
   return CBS_OK;
 }
 

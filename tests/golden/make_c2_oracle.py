@@ -1,0 +1,49 @@
+"""Write oracle eigenvalues for the 32x32x16 workload at two energies.
+
+Runs only the CPU oracle (oracle/) on the seeded synthetic inputs and stores, per
+energy, the kept eigenvalues, their residuals, the numerical rank and the BiCG
+iteration counts in tests/golden/c2_oracle.npz.  The quadrature points are solved in parallel worker
+processes (spawned); a few minutes per energy on 8 cores.
+
+    python tests/golden/make_c2_oracle.py
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import ss  # noqa: E402
+from oracle.operator import CellOperator  # noqa: E402
+from paper_1709_09347_gb300 import synth  # noqa: E402
+
+ENERGY_INDEX = (7, 12)
+
+
+def main():
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    pool = cf.ProcessPoolExecutor(max_workers=os.cpu_count(), mp_context=mp.get_context("spawn"))
+    wl = synth.workload("c2")
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    out = {"energy_index": np.array(ENERGY_INDEX), "energies": wl.energies[list(ENERGY_INDEX)]}
+    for e in ENERGY_INDEX:
+        E = float(wl.energies[e])
+        t = time.time()
+        r = ss.ss_hankel(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, delta=wl.delta, tol=1e-10,
+                         pool=pool)
+        print(f"E={E:+.4f}: {len(r.lam)} kept, rank {r.rank}, iters {r.iters.max()}, "
+              f"{time.time() - t:.0f} s", flush=True)
+        out[f"lam_{e}"] = r.lam
+        out[f"res_{e}"] = r.residual
+        out[f"rank_{e}"] = np.array(r.rank)
+        out[f"iters_{e}"] = r.iters
+    np.savez(os.path.join(os.path.dirname(os.path.abspath(__file__)), "c2_oracle.npz"), **out)
+
+
+if __name__ == "__main__":
+    main()
