@@ -6,8 +6,8 @@ moments, Hankel SVD + reduced eigenproblem, residual filter, k) for every energy
 workload, through libcbs's C ABI.  Default workload: the 32x32x16 molecular-crystal
 cell (8th-order FD, 40 atoms with 4 projectors each, 16 energies in [-0.5, 0.5] Ha,
 N_int = 32 per circle, L = 32, M = 8) in plain FP64 — the configuration the metric is
-quoted on.  The complex64 + FP64-refinement form is measured on the same workload and
-reported beside it.
+quoted on.  The headline is the complex64 BiCG + FP64 iterative refinement form; the plain
+FP64 form is measured on the same workload and reported beside it ("fp64").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl reference]
 
@@ -214,7 +214,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-warmup", type=int, default=1)
     args = ap.parse_args()
     world, rank, local = _dist()
 
@@ -273,60 +275,71 @@ def main():
         ms = max_over_ranks(ev0.elapsed_time(ev1))
         return ms, results, clk.summary(), launches
 
-    ms, results, clocks, launches = timed("fp64", args.steps, args.warmup)
-    value = args.steps * n_e * world / (ms / 1e3)
-
-    # eigenpair bookkeeping of the timed steps
-    last = results[-1]
-    kept = [len(e["lam"]) for e in last.energies]
-    worst_res = max([float(np.max(e["residual"])) for e in last.energies if len(e["residual"])] or [0.0])
-    flags = sorted({e["flags"] for e in last.energies})
-    prof = {k: sum(r.profile[k][f] for r in results) for k in ("c128",) for f in ("ms",)}
-    p128 = {f: sum(r.profile["c128"][f] for r in results) for f in ("ms", "launches", "outputs")}
-    flops = flops_per_output(wl)
-    achieved_tflops = p128["outputs"] * flops / (p128["ms"] / 1e3) / 1e12 if p128["ms"] else None
+    hbm, hbm_src = _peaks()
     sha = _apply_sha()
-    traffic = None
-    if APPLY_TRAFFIC["sha"] == sha and APPLY_TRAFFIC["c128_bytes_per_output"]:
-        traffic = APPLY_TRAFFIC["c128_bytes_per_output"] * p128["outputs"] / p128["launches"]
-    roofline = {
-        "kernel": "k_apply_zm<double> (+k_proj_gather<double>): stencil + projector apply, FP64",
-        "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved_tflops / FP64_PEAK_TFLOPS if achieved_tflops else None,
-        "traffic": traffic, "peak_source": "nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
-        "flops_per_output": flops, "outputs": p128["outputs"], "launches": p128["launches"],
-        "avg_launch_ms": p128["ms"] / max(p128["launches"], 1),
-        "share_of_step": p128["ms"] / ms if ms else None,
-    }
 
-    # complex64 BiCG + FP64 refinement on the same workload
-    mixed = None
-    if not args.no_mixed:
-        ms2, res2, clocks2, launches2 = timed("fp32_refine", args.steps, 1)
-        hbm, hbm_src = _peaks()
-        p64 = {f: sum(r.profile["c64"][f] for r in res2) for f in ("ms", "launches", "outputs")}
-        bpo = bytes_per_output(wl, 8)
-        ach = p64["outputs"] * bpo / (p64["ms"] / 1e3) / 1e9 if p64["ms"] else None
-        kept2 = [len(e["lam"]) for e in res2[-1].energies]
-        mixed = {
-            "value": args.steps * n_e * world / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / args.steps,
-            "dtype": "c64 BiCG + f64 refinement", "kept_per_energy": kept2,
-            "same_count_as_fp64": kept2 == kept,
-            "max_residual": max([float(np.max(e["residual"])) for e in res2[-1].energies if len(e["residual"])] or [0.0]),
-            "roofline": {"kernel": "k_apply_zm<float> (+k_proj_gather<float>): stencil + projector apply, complex64",
-                         "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                         "frac": ach / hbm if ach else None, "traffic": None,
-                         "peak_source": hbm_src, "bytes_per_output": bpo,
-                         "avg_launch_ms": p64["ms"] / max(p64["launches"], 1)},
-            "clocks": clocks2, "gpu_launches": launches2,
-        }
+    def roofline_for(results, precision, ms_total):
+        key = "c64" if precision == "fp32_refine" else "c128"
+        p = {f: sum(r.profile[key][f] for r in results) for f in ("ms", "launches", "outputs")}
+        if not p["ms"]:
+            return None
+        s = 8 if key == "c64" else 16
+        rl = {"kernel": f"k_apply_zm + k_proj_gather ({'complex64' if s == 8 else 'complex128'}): "
+                        "stencil + projector operator apply",
+              "outputs": p["outputs"], "launches": p["launches"],
+              "avg_launch_ms": p["ms"] / max(p["launches"], 1),
+              "share_of_step": p["ms"] / ms_total if ms_total else None}
+        traffic = None
+        tkey = f"{key}_bytes_per_output"
+        if APPLY_TRAFFIC["sha"] == sha and APPLY_TRAFFIC.get(tkey):
+            traffic = APPLY_TRAFFIC[tkey] * p["outputs"] / max(p["launches"], 1)
+        if key == "c64":
+            bpo = bytes_per_output(wl, 8)
+            ach = p["outputs"] * bpo / (p["ms"] / 1e3) / 1e9
+            rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                      traffic=traffic, peak_source=hbm_src, bytes_per_output=bpo,
+                      bytes_per_launch=bpo * p["outputs"] / max(p["launches"], 1))
+        else:
+            fpo = flops_per_output(wl)
+            ach = p["outputs"] * fpo / (p["ms"] / 1e3) / 1e12
+            rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                      frac=ach / FP64_PEAK_TFLOPS, traffic=traffic,
+                      peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
+                      flops_per_output=fpo, flops_per_launch=fpo * p["outputs"] / max(p["launches"], 1))
+        return rl
+
+    def summary(results):
+        last = results[-1]
+        kept = [len(e["lam"]) for e in last.energies]
+        worst = max([float(np.max(e["residual"])) for e in last.energies if len(e["residual"])] or [0.0])
+        return last, kept, worst, sorted({e["flags"] for e in last.energies})
+
+    # headline: complex64 BiCG inside FP64 refinement
+    ms, results, clocks, launches = timed("fp32_refine", args.steps, args.warmup)
+    value = args.steps * n_e * world / (ms / 1e3)
+    last, kept, worst_res, flags = summary(results)
+    roofline = roofline_for(results, "fp32_refine", ms)
+
+    # comparison: plain FP64 BiCG on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        ms64, res64, clocks64, launches64 = timed("fp64", args.fp64_steps, args.fp64_warmup)
+        last64, kept64, worst64, flags64 = summary(res64)
+        fp64 = {"value": args.fp64_steps * n_e * world / (ms64 / 1e3), "unit": UNIT,
+                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                "warmup": args.fp64_warmup, "dtype": "f64", "kept_per_energy": kept64,
+                "same_count_as_headline": kept64 == kept, "max_residual": worst64, "flags": flags64,
+                "roofline": roofline_for(res64, "fp64", ms64), "clocks": clocks64,
+                "gpu_launches": launches64,
+                "stage_ms_last_step": {"solve": last64.ms_solve, "moments": last64.ms_moments,
+                                       "extract": last64.ms_extract}}
 
     # end to end through the C ABI with host buffers: Hamiltonian upload, V upload,
     # solve, results (eigenvalues, k, residuals, eigenvectors) back to the host
     def e2e_step():
         Hh = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
         r = cbs.solve(Hh, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
-                      cbs.options(precision="fp64", tol=wl.tol, delta=wl.delta))
+                      cbs.options(precision="fp32_refine", tol=wl.tol, delta=wl.delta))
         Hh.close()
         return r
     e2e_steps = 1
@@ -348,7 +361,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline_sample(args.workload, 2, 7)
+            cpu = cpu_baseline_sample(args.workload, 1, 7)
         except Exception as ex:  # noqa: BLE001
             cpu = {"error": str(ex)[-300:]}
 
@@ -356,16 +369,17 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 BiCG + f64 refinement",
+            "data": "synthetic",
             "config": {"workload": f"{args.workload}: {wl.grid.nx}x{wl.grid.ny}x{wl.grid.nz} cell, "
                                    f"FD{wl.grid.fd_order}, "
                                    f"{wl.projectors.n_atoms if wl.projectors else 0} atoms x 4 projectors, "
                                    f"{n_e} energies, N_int={wl.n_int}, L={wl.L}, M={wl.M}, "
-                                   f"lambda_min={wl.lambda_min}, BiCG tol {wl.tol:g}, plain FP64",
+                                   f"lambda_min={wl.lambda_min}, BiCG tol {wl.tol:g}",
                        "energies_per_step": n_e, "l2": "state per step >> L2 (no flush needed)",
                        "kept_per_energy": kept, "max_residual": worst_res, "flags": flags},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
-            "cpu_baseline": cpu, "fp32_refine": mixed,
+            "cpu_baseline": cpu, "fp64": fp64,
             "stage_ms_last_step": {"solve": last.ms_solve, "moments": last.ms_moments,
                                    "extract": last.ms_extract},
         }

@@ -97,8 +97,12 @@ typedef struct {
   int precision;        /* CBS_FP64 or CBS_FP32_REFINE                                   */
   int extraction;       /* CBS_HANKEL (Algorithm 1) or CBS_RR (Rayleigh-Ritz)            */
   int check_every;      /* BiCG iterations per CUDA-graph replay between host polls (8)  */
-  double inner_tol;     /* FP32 inner solve tolerance relative to the outer residual (1e-4) */
-  int max_sweeps;       /* FP64 refinement sweeps (12)                                   */
+  double inner_tol;     /* complex64 phase ends when ||r|| < inner_tol * max ||r|| since the
+                           last FP64 residual update (0.1)                                */
+  int max_sweeps;       /* FP64 residual updates (residual replacements) (200)           */
+  int inner_max_iter;   /* iteration cap of one complex64 phase (1000)                   */
+  int stall_sweeps;     /* updates without halving the FP64 residual before the columns
+                           left are finished by FP64 BiCG (4)                              */
   int energies_per_batch; /* energies solved together; 0 = as many as fit (0)            */
   int profile;          /* 1: time every operator-apply launch with CUDA events (0)      */
   void *stream;         /* cudaStream_t to run on; NULL = the library's own stream       */
@@ -168,7 +172,8 @@ typedef struct {
   int n_kept;           /* eigenpairs passing the ring and residual filter             */
   int max_iters;        /* largest BiCG iteration count over the energy's systems      */
   int sweeps;           /* FP64 refinement sweeps (0 for plain FP64)                   */
-  int flags;            /* bit 0: not converged, bit 1: breakdown, bit 2: rank saturated */
+  int flags;            /* bit 0: not converged, bit 1: breakdown, bit 2: rank saturated,
+                           bit 3/4: SVD/eigen-solver iteration limit, bit 5: FP64 continuation */
   double sigma_max, sigma_cut; /* sigma_1 and the smallest kept singular value          */
   double max_solve_residual;   /* max over systems/columns of ||V - P(z)Y||/||V|| (FP64) */
 } cbs_stats;

@@ -41,8 +41,10 @@ extern "C" cbs_status cbs_options_default(cbs_options *o) {
   o->precision = CBS_FP64;
   o->extraction = CBS_HANKEL;
   o->check_every = 8;
-  o->inner_tol = 1e-4;
-  o->max_sweeps = 12;
+  o->inner_tol = 0.1;
+  o->max_sweeps = 200;
+  o->inner_max_iter = 1000;
+  o->stall_sweeps = 4;
   o->energies_per_batch = 0;
   o->stream = nullptr;
   return CBS_OK;

@@ -49,17 +49,35 @@ __global__ void k_proj_gather(HamView H, int L, const typename CT<R>::T *__restr
   const R *pv = pval_ptr<R>(H);
   const int64_t t0 = H.sup_ptr[a], t1 = H.sup_ptr[a + 1];
   const C *Xs = X + (int64_t)s * H.n * L;
-  for (int64_t t = t0 + ly; t < t1; t += py) {
-    C xv = Xs[(int64_t)H.sup_idx[t] * L + c];
-    int m = H.sup_wrap[t];
-    C f = (m == 0) ? xv : (m > 0 ? cmul(wi, xv) : cmul(w, xv));   // w^{-m} x
+  // four independent support entries per step keep several gathers in flight
+  constexpr int U = 4;
+  for (int64_t tb = t0 + ly; tb < t1; tb += (int64_t)U * py) {
+    C xv[U];
+    int mw[U];
 #pragma unroll
-    for (int mu = 0; mu < kMaxProj; ++mu)
-      if (mu < np) {
-        R p = pv[t * np + mu];
-        acc[mu].x += p * f.x;
-        acc[mu].y += p * f.y;
+    for (int u = 0; u < U; ++u) {
+      const int64_t t = tb + (int64_t)u * py;
+      if (t < t1) {
+        xv[u] = Xs[(int64_t)H.sup_idx[t] * L + c];
+        mw[u] = H.sup_wrap[t];
+      } else {
+        xv[u] = mk<R>(0, 0);
+        mw[u] = 0;
       }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t t = tb + (int64_t)u * py;
+      if (t >= t1) break;
+      const C f = (mw[u] == 0) ? xv[u] : (mw[u] > 0 ? cmul(wi, xv[u]) : cmul(w, xv[u]));  // w^{-m} x
+#pragma unroll
+      for (int mu = 0; mu < kMaxProj; ++mu)
+        if (mu < np) {
+          const R p = pv[t * np + mu];
+          acc[mu].x += p * f.x;
+          acc[mu].y += p * f.y;
+        }
+    }
   }
   for (int mu = 0; mu < np; ++mu) red[((int64_t)ly * np + mu) * L + c] = acc[mu];
   __syncthreads();
@@ -143,8 +161,10 @@ __global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typena
 #pragma unroll
   for (int d = 0; d < 2 * MH; ++d) q[d] = bloch(d - MH);
   for (int iz = 0; iz < nz; ++iz) {
-    q[2 * MH] = bloch(iz + MH);
     const int pt = iz * nxy + line;
+    int e0 = 0, e1 = 0;
+    if (D) { e0 = (int)H.pt_ptr[pt]; e1 = (int)H.pt_ptr[pt + 1]; }   // issued early
+    q[2 * MH] = bloch(iz + MH);
     const int b = pt * L + c;
     const C x0 = q[MH];
     const R dd = dk + vl[pt];
@@ -158,7 +178,6 @@ __global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typena
       acc.y += wx[k] * (a1.y + a2.y) + wy[k] * (b1.y + b2.y) + wz[k] * (z1.y + z2.y);
     }
     if (D) {
-      const int e0 = (int)H.pt_ptr[pt], e1 = (int)H.pt_ptr[pt + 1];
       for (int qq = e0; qq < e1; ++qq) {
         const int t = H.pt_ent[qq], a = H.pt_atom[qq];
         const C *Da = D + (((int64_t)s * H.n_atoms + a) * np) * L + c;

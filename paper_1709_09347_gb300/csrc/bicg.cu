@@ -18,6 +18,8 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include "bicg.cuh"
 
 namespace cbs {
@@ -63,17 +65,26 @@ __global__ void k_init(int n, int64_t N, int L, int chunk_pts, int n_chunks, con
 }
 
 __global__ void k_reduce_init(int n, int L, int n_chunks, const double *part, double2 *rho,
-                              double2 *beta, double *nb, double *nbd, int *active, int *iters,
-                              int *flags, const int *colmask, int *sys_active, int *n_active) {
+                              double2 *rho_prev, double2 *beta, double *nb, double *nbd,
+                              double *tgt, double *tgtd, double *rmax, double *rmaxd, double tfloor,
+                              const double *ref_norm, int *active, int *iters, int *flags,
+                              const int *colmask, int *sys_active, int *n_active) {
   const int s = blockIdx.x, c = threadIdx.x;
   const int64_t k = (int64_t)s * L + c;
   double a[4] = {0, 0, 0, 0};
   for (int ch = 0; ch < n_chunks; ++ch)
     for (int q = 0; q < 4; ++q) a[q] += part[(((int64_t)s * n_chunks + ch) * L + c) * 4 + q];
   rho[k] = make_double2(a[0], a[1]);
+  rho_prev[k] = make_double2(0, 0);
   beta[k] = make_double2(0, 0);
   nb[k] = sqrt(a[2]);
   nbd[k] = sqrt(a[3]);
+  // absolute targets: relative to this right-hand side, or to reference norms
+  // ref_norm[2n][L] (primal then dual) when the system solves for a correction
+  tgt[k] = tfloor * (ref_norm ? ref_norm[k] : nb[k]);
+  tgtd[k] = tfloor * (ref_norm ? ref_norm[(int64_t)n * L + k] : nbd[k]);
+  rmax[k] = nb[k];
+  rmaxd[k] = nbd[k];
   int act = (colmask ? colmask[k] : 1) && a[2] > 0 && a[3] > 0;
   active[k] = act;
   iters[k] = 0;
@@ -185,8 +196,9 @@ __global__ void k_pass_b(int n, int64_t N, int L, int chunk_pts, int n_chunks,
 }
 
 __global__ void k_reduce_beta(int n, int L, int n_chunks, const double *part, double2 *rho,
-                              double2 *beta, const double *nb, const double *nbd, int *active,
-                              int *iters, int *flags, double tol, int max_iter, int *sys_active,
+                              double2 *rho_prev, double2 *beta, const double *tgt,
+                              const double *tgtd, double *rmax, double *rmaxd, double tfac,
+                              int *active, int *iters, int *flags, int max_iter, int *sys_active,
                               int *n_active) {
   const int s = blockIdx.x, c = threadIdx.x;
   if (!sys_active[s]) return;   // uniform per block
@@ -198,23 +210,92 @@ __global__ void k_reduce_beta(int n, int L, int n_chunks, const double *part, do
       for (int q = 0; q < 4; ++q) a[q] += part[(((int64_t)s * n_chunks + ch) * L + c) * 4 + q];
     const int it = iters[k] + 1;
     iters[k] = it;
-    const double rel = sqrt(a[2]) / nb[k], reld = sqrt(a[3]) / nbd[k];
+    const double nr = sqrt(a[2]), nrd = sqrt(a[3]);
     const double2 rn = make_double2(a[0], a[1]);
-    if (rel <= tol && reld <= tol) {
+    const double2 rold = rho[k];
+    rho_prev[k] = rold;                  // kept for a later residual replacement
+    rho[k] = rn;
+    // stop (or pause until the next residual replacement) below max(tfac * the largest
+    // residual norm since the last replacement, the absolute target)
+    const double mx = fmax(rmax[k], nr), mxd = fmax(rmaxd[k], nrd);
+    rmax[k] = mx;
+    rmaxd[k] = mxd;
+    if (nr <= fmax(tfac * mx, tgt[k]) && nrd <= fmax(tfac * mxd, tgtd[k])) {
       act = 0;
-    } else if (!isfinite(rel) || !isfinite(reld) || !(cabs2(rn) > 0)) {
+    } else if (!isfinite(nr) || !isfinite(nrd) || !(cabs2(rn) > 0)) {
       flags[k] |= 2;
       act = 0;
     } else if (it >= max_iter) {
       flags[k] |= 1;
       act = 0;
     } else {
-      beta[k] = cdiv(rn, rho[k]);
-      rho[k] = rn;
+      beta[k] = cdiv(rn, rold);
     }
     active[k] = act;
   }
   if (!act) beta[k] = make_double2(0, 0);
+  int any = __syncthreads_or(act);
+  if (c == 0) {
+    sys_active[s] = any;
+    sys_active[n + s] = any;
+    if (any) atomicAdd(n_active, 1);
+  }
+}
+
+// Residual replacement (mixed precision): the recursive residuals of the columns that
+// still need work are replaced by the FP64 true residuals R = B - P(z)Y (rounded to the
+// working type), the correction x restarts from zero (it has been added to Y), and the
+// search directions p, p~ are kept.  Partial sums give rho' = (r~', r'), ||r'||, ||r~'||.
+template <typename R>
+__global__ void k_replace(int n, int64_t N, int L, int chunk_pts, int n_chunks,
+                          const double2 *R64, const int *colmask, typename CT<R>::T *x,
+                          typename CT<R>::T *r, double *part) {
+  typedef typename CT<R>::T C;
+  const int s = blockIdx.y, chunk = blockIdx.x, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
+  const int64_t k = (int64_t)s * L + c;
+  const bool need = colmask[k];
+  double acc[4] = {0, 0, 0, 0};
+  const int64_t i0 = (int64_t)chunk * chunk_pts;
+  const int64_t i1 = min(N, i0 + chunk_pts);
+  for (int64_t i = i0 + ly; i < i1; i += py) {
+    const int64_t e = ((int64_t)s * N + i) * L + c, ed = ((int64_t)(n + s) * N + i) * L + c;
+    x[e] = mk<R>(0, 0);
+    x[ed] = mk<R>(0, 0);
+    if (need) {
+      const C b = from_d<R>(R64[e]), bd = from_d<R>(R64[ed]);
+      r[e] = b;
+      r[ed] = bd;
+      const double2 bb = to_d(b), bdd = to_d(bd);
+      acc[0] += bdd.x * bb.x + bdd.y * bb.y;
+      acc[1] += bdd.x * bb.y - bdd.y * bb.x;
+      acc[2] += cabs2(bb);
+      acc[3] += cabs2(bdd);
+    }
+  }
+  block_partials<R>(acc, part, (int64_t)s * n_chunks + chunk);
+}
+
+__global__ void k_reduce_replace(int n, int L, int n_chunks, const double *part, double2 *rho,
+                                 const double2 *rho_prev, double2 *beta, double *rmax, double *rmaxd,
+                                 int *active, const int *colmask, int *sys_active, int *n_active) {
+  const int s = blockIdx.x, c = threadIdx.x;
+  const int64_t k = (int64_t)s * L + c;
+  int act = colmask[k];
+  if (act) {
+    double a[4] = {0, 0, 0, 0};
+    for (int ch = 0; ch < n_chunks; ++ch)
+      for (int q = 0; q < 4; ++q) a[q] += part[(((int64_t)s * n_chunks + ch) * L + c) * 4 + q];
+    const double2 rn = make_double2(a[0], a[1]);
+    const double2 rp = rho_prev[k];
+    beta[k] = (cabs2(rp) > 0) ? cdiv(rn, rp) : make_double2(0, 0);
+    rho[k] = rn;
+    rmax[k] = sqrt(a[2]);
+    rmaxd[k] = sqrt(a[3]);
+    if (!(cabs2(rn) > 0) || !isfinite(a[2]) || !isfinite(a[3])) { act = 0; beta[k] = make_double2(0, 0); }
+  } else {
+    beta[k] = make_double2(0, 0);
+  }
+  active[k] = act;
   int any = __syncthreads_or(act);
   if (c == 0) {
     sys_active[s] = any;
@@ -262,7 +343,7 @@ size_t Bicg<R>::bytes_needed(const HamView &H, int n, int L) {
   int64_t b = 4 * align256(vec);
   b += align256((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * sizeof(C));
   b += align256((int64_t)2 * n * sizeof(double2)) + align256((int64_t)2 * n * sizeof(double));
-  b += 3 * align256((int64_t)n * L * sizeof(double2)) + 2 * align256((int64_t)n * L * sizeof(double));
+  b += 4 * align256((int64_t)n * L * sizeof(double2)) + 6 * align256((int64_t)n * L * sizeof(double));
   b += 3 * align256((int64_t)n * L * sizeof(int)) + align256((int64_t)2 * n * sizeof(int)) + 256;
   b += align256((int64_t)n * nc * L * 4 * sizeof(double)) + 256;
   return (size_t)b;
@@ -289,6 +370,11 @@ cbs_status Bicg<R>::alloc(const HamView &H_, int n_, int L_) {
   rho = (double2 *)take((int64_t)n * L * sizeof(double2));
   alpha = (double2 *)take((int64_t)n * L * sizeof(double2));
   beta = (double2 *)take((int64_t)n * L * sizeof(double2));
+  rho_prev = (double2 *)take((int64_t)n * L * sizeof(double2));
+  tgt = (double *)take((int64_t)n * L * sizeof(double));
+  tgtd = (double *)take((int64_t)n * L * sizeof(double));
+  rmax = (double *)take((int64_t)n * L * sizeof(double));
+  rmaxd = (double *)take((int64_t)n * L * sizeof(double));
   nb = (double *)take((int64_t)n * L * sizeof(double));
   nbd = (double *)take((int64_t)n * L * sizeof(double));
   active = (int *)take((int64_t)n * L * sizeof(int));
@@ -331,15 +417,18 @@ static size_t red_smem(int L) {
 
 template <typename R>
 cbs_status Bicg<R>::init(const double2 *B, int64_t bstride, const double2 *Bd, int64_t bdstride,
-                         const int *colmask, cudaStream_t st) {
+                         const int *colmask, double tfloor, double tfac_, cudaStream_t st,
+                         const double *ref_norm) {
+  tfac = tfac_;
   dim3 blk = col_block(L);
   dim3 grd((unsigned)n_chunks, (unsigned)n, 1);
   k_init<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, B, bstride, Bd, bdstride,
                                           x, r, p, part); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   CBS_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
-  k_reduce_init<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, beta, nb, nbd, active, iters, flags,
-                                 colmask, sys_active, n_active); cbs::count_launches(1);
+  k_reduce_init<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, rho_prev, beta, nb, nbd, tgt, tgtd, rmax,
+                                 rmaxd, tfloor, ref_norm, active, iters, flags, colmask, sys_active,
+                                 n_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
@@ -351,10 +440,11 @@ cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st, int kk) {
   k_update_p<R><<<grd, blk, 0, st>>>(n, N, L, chunk_pts, r, p, beta, active, sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   const bool prof = profile && kk >= 0 && 2 * kk + 1 < n_prof_ev;
-  if (prof) CBS_CUDA(cudaEventRecord(prof_ev[2 * kk], st));
+  // recorded as real event nodes of the graph (not capture-dependency markers)
+  if (prof) CBS_CUDA(cudaEventRecordWithFlags(prof_ev[2 * kk], st, cudaEventRecordExternal));
   cbs_status s = apply_P<R>(H, 2 * n, L, p, q, tw, false, E, D, sys_active, st);
   if (s != CBS_OK) return s;
-  if (prof) CBS_CUDA(cudaEventRecord(prof_ev[2 * kk + 1], st));
+  if (prof) CBS_CUDA(cudaEventRecordWithFlags(prof_ev[2 * kk + 1], st, cudaEventRecordExternal));
   k_dot_pq<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, p, q, part, sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   k_reduce_alpha<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, alpha, active, flags, sys_active,
@@ -364,15 +454,15 @@ cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st, int kk) {
                                              active, part, sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   CBS_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
-  k_reduce_beta<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, beta, nb, nbd, active, iters, flags,
-                                 tol, max_iter, sys_active, n_active); cbs::count_launches(1);
+  k_reduce_beta<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, rho_prev, beta, tgt, tgtd, rmax, rmaxd,
+                                 tfac, active, iters, flags, max_iter, sys_active, n_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
 
 template <typename R>
 cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStream_t st,
-                            int *host_iters_done) {
+                            int *host_iters_done, int call_cap) {
   if (check_every < 1) check_every = 1;
   if (profile && n_prof_ev == 0) {
     const int ne = 2 * (check_every < 64 ? check_every : 64);
@@ -400,7 +490,8 @@ cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStrea
   s = CBS_OK;
   // every replay advances all still-active columns by check_every iterations; max_iter is
   // also enforced per column on the device, so the loop ends within max_iter/check_every + 1
-  const int max_replays = max_iter / check_every + 2;
+  int max_replays = max_iter / check_every + 2;
+  if (call_cap > 0) max_replays = std::min(max_replays, (call_cap + check_every - 1) / check_every);
   for (int rep = 0; rep < max_replays; ++rep) {
     ce = cudaGraphLaunch(exec, st);
     count_launches(per_graph);
@@ -413,6 +504,8 @@ cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStrea
         if (cudaEventElapsedTime(&ms, prof_ev[2 * k], prof_ev[2 * k + 1]) == cudaSuccess) {
           prof_ms += ms;
           prof_launches += 1;
+        } else {
+          (void)cudaGetLastError();   // do not leave a sticky error for the next check
         }
       }
     }
@@ -423,6 +516,21 @@ cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStrea
   cudaGraphExecDestroy(exec);
   if (host_iters_done) *host_iters_done = done;
   return s;
+}
+
+template <typename R>
+cbs_status Bicg<R>::replace(const double2 *R64, const int *colmask, cudaStream_t st) {
+  dim3 blk = col_block(L);
+  dim3 grd((unsigned)n_chunks, (unsigned)n, 1);
+  k_replace<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, R64, colmask, x, r, part);
+  cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  CBS_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+  k_reduce_replace<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, rho_prev, beta, rmax, rmaxd, active,
+                                    colmask, sys_active, n_active);
+  cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
 }
 
 template struct Bicg<double>;
@@ -463,6 +571,19 @@ cbs_status launch_residual(int n2, int64_t N, int L, const double2 *B, int64_t b
   dim3 grd(64, (unsigned)n2, 1);
   k_residual<<<grd, blk, (size_t)blk.x * blk.y * sizeof(double), st>>>(n, N, L, B, bstride, Bd,
                                                                         bdstride, AY, colnorm2); cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+__global__ void k_accumulate64(int64_t count, double2 *Y, const double2 *X) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    Y[e] = cadd(Y[e], X[e]);
+}
+
+cbs_status launch_accumulate(int64_t count, double2 *Y, const double2 *X, cudaStream_t st) {
+  k_accumulate64<<<152 * 8, 256, 0, st>>>(count, Y, X);
+  cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }

@@ -18,6 +18,10 @@ struct Bicg {
   double2 *tw = nullptr;                                      // [2n]
   double *E = nullptr;                                        // [2n]
   double2 *rho = nullptr, *alpha = nullptr, *beta = nullptr;  // [n][L]
+  double2 *rho_prev = nullptr;                                // [n][L]
+  double *tgt = nullptr, *tgtd = nullptr;                     // [n][L] absolute stop targets
+  double *rmax = nullptr, *rmaxd = nullptr;                   // [n][L] max ||r|| since (re)start
+  double tfac = 0;                                            // relative pause factor
   double *nb = nullptr, *nbd = nullptr;                       // [n][L]
   int *active = nullptr, *iters = nullptr, *flags = nullptr;  // [n][L]
   int *sys_active = nullptr;                                  // [2n]
@@ -38,12 +42,19 @@ struct Bicg {
   // Set twists/energies: primal twist z[s], dual twist 1/conj(z[s]); z, E on device.
   cbs_status set_systems(const double2 *z, const double *Es, cudaStream_t st);
   // Initialise with primal RHS B (stride bstride elements between systems, 0 = shared)
-  // and dual RHS Bd; columns with colmask == 0 (if colmask) start inactive.
+  // and dual RHS Bd; columns with colmask == 0 (if colmask) start inactive.  A column
+  // stops when ||r|| <= max(tfac * max||r|| since the (re)start, tfloor ||b||), and the
+  // same for the dual (tfac = 0: plain tolerance tfloor).
   cbs_status init(const double2 *B, int64_t bstride, const double2 *Bd, int64_t bdstride,
-                  const int *colmask, cudaStream_t st);
-  // Iterate until every column converged, broke down or reached max_iter.
+                  const int *colmask, double tfloor, double tfac, cudaStream_t st,
+                  const double *ref_norm = nullptr);
+  // Iterate until every column reached its target, broke down or reached max_iter
+  // iterations in total; call_cap > 0 bounds the iterations of this call.
   cbs_status iterate(double tol, int max_iter, int check_every, cudaStream_t st,
-                     int *host_iters_done);
+                     int *host_iters_done, int call_cap = 0);
+  // Residual replacement from FP64 true residuals R64 [2n][N][L]; columns with
+  // colmask != 0 resume from them.
+  cbs_status replace(const double2 *R64, const int *colmask, cudaStream_t st);
   // one iteration (captured into graphs); k indexes the iteration inside the graph
   cbs_status step(double tol, int max_iter, cudaStream_t st, int k);
   // outputs written by the apply launches so far (2 * active systems * N * L)
@@ -57,6 +68,7 @@ cbs_status launch_residual(int n2, int64_t N, int L, const double2 *B, int64_t b
                            double *colnorm2 /*[2n][L]*/, cudaStream_t st);
 // Y[2n] += (double) X32[2n]
 cbs_status launch_accumulate(int64_t count, double2 *Y, const float2 *X, cudaStream_t st);
+cbs_status launch_accumulate(int64_t count, double2 *Y, const double2 *X, cudaStream_t st);
 // X[2n] (type C) copies of Y (double) are not needed; zero fill helper
 cbs_status launch_twists(int n, const double2 *z, const double *E, double2 *tw, double *E2,
                          cudaStream_t st);

@@ -123,10 +123,12 @@ void count_launches(uint64_t n);
 void uncount_launches(uint64_t n);   // kernels recorded into a graph, not run
 uint64_t launches_so_far();
 
-#define CBS_CUDA(call)                                   \
-  do {                                                   \
-    cudaError_t _e = (call);                             \
-    if (_e != cudaSuccess) return cbs::cuda_fail(_e, #call); \
+#define CBS_STR2(x) #x
+#define CBS_STR(x) CBS_STR2(x)
+#define CBS_CUDA(call)                                                               \
+  do {                                                                               \
+    cudaError_t _e = (call);                                                         \
+    if (_e != cudaSuccess) return cbs::cuda_fail(_e, __FILE__ ":" CBS_STR(__LINE__) ": " #call); \
   } while (0)
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

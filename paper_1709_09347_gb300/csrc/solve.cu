@@ -182,6 +182,7 @@ struct ShiftedSolver {
   std::vector<int> iters, flags;
   std::vector<double> maxrel;
   int sweeps = 0;
+  bool fp64_continued = false;
   double prof_ms[2] = {0, 0}, prof_launches[2] = {0, 0}, prof_outputs[2] = {0, 0};
   cbs_status collect_profile(cudaStream_t st) {
     double o64 = 0, o32 = 0;
@@ -201,7 +202,7 @@ struct ShiftedSolver {
   static size_t bytes_per_system(const HamView &H, int L, int precision) {
     const size_t v16 = (size_t)H.n * L * 16;
     if (precision == CBS_FP64) return 2 * (4 * v16 + v16) + 2 * v16;   // state + residual check
-    return 2 * (4 * v16 / 2) + 2 * v16 + 2 * v16 + 2 * v16;             // f32 state, Y, R
+    return 2 * (4 * v16 / 2) + 2 * v16 + 2 * v16 + 2 * v16;             // f32 state, Y, R, D
   }
 
   cbs_status run(const HamView &H_, int n_, int L_, const double2 *zs, const double *Es,
@@ -217,7 +218,7 @@ struct ShiftedSolver {
     if (o.precision == CBS_FP64) {
       CBS_TRY(b64.alloc(H, n, L));
       CBS_TRY(b64.set_systems(zs, Es, st));
-      CBS_TRY(b64.init(B, 0, B, 0, nullptr, st));
+      CBS_TRY(b64.init(B, 0, B, 0, nullptr, o.tol, 0.0, st));
       int done = 0;
       CBS_TRY(b64.iterate(o.tol, o.max_iter, o.check_every, st, &done));
       Y = b64.x;
@@ -229,34 +230,72 @@ struct ShiftedSolver {
       sweeps = 0;
       return collect_profile(st);
     }
-    // complex64 BiCG inside FP64 iterative refinement:
-    //   R = B - P(z) Y, R~ = B - P(z)^dagger Y~  (FP64)
-    //   solve P(z) D = R, P(z)^dagger D~ = R~ in complex64 to inner_tol
-    //   Y += D, Y~ += D~  (FP64), until every column meets tol.
+    // complex64 BiCG with FP64 refinement of the residual (reliable updates):
+    //   the complex64 recursion runs until its residual is below inner_tol times the
+    //   largest residual norm seen since the last update (or inner_max_iter iterations);
+    //   its correction is added to Y in FP64, the true residuals R = B - P(z) Y and
+    //   R~ = B - P(z)^dagger Y~ are formed in FP64, and the columns above tol continue
+    //   from R (rounded) with their search directions kept.
     CBS_TRY(ybuf.alloc((size_t)2 * n * H.n * L * sizeof(double2)));
     Y = ybuf.as<double2>();
     CBS_CUDA(cudaMemsetAsync(Y, 0, (size_t)2 * n * H.n * L * sizeof(double2), st));
     CBS_TRY(b32.alloc(H, n, L));
     CBS_TRY(b32.set_systems(zs, Es, st));
     sweeps = 0;
-    for (int sw = 0; sw <= o.max_sweeps; ++sw) {
-      int unconv = 0;
-      CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));
-      if (unconv == 0 || sw == o.max_sweeps) break;
-      // inner solve on the residuals (rc.R holds B - AY for primal and dual)
-      CBS_TRY(b32.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
-                       rc.colmask, st));
+    int unconv = 0;
+    CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));   // R = B
+    CBS_TRY(b32.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
+                     rc.colmask, 0.25 * o.tol, o.inner_tol, st));
+    std::vector<double> rel((size_t)n * L);
+    std::vector<int> need((size_t)n * L);
+    double best = 1e300;
+    int stall = 0;
+    for (int sw = 0; sw < o.max_sweeps && unconv > 0; ++sw) {
       int done = 0;
-      CBS_TRY(b32.iterate(o.inner_tol, o.max_iter, o.check_every, st, &done));
+      CBS_TRY(b32.iterate(o.tol, o.max_iter, o.check_every, st, &done, o.inner_max_iter));
       CBS_TRY(launch_accumulate((int64_t)2 * n * H.n * L, Y, b32.x, st));
-      CBS_CUDA(cudaMemcpyAsync(it_tmp.data(), b32.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), b32.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));
+      ++sweeps;
+      if (unconv == 0) break;
+      // stagnation of the FP64 true residual: the single-precision recursion no longer
+      // makes progress on the columns that are left (loss of bi-orthogonality)
+      CBS_CUDA(cudaMemcpyAsync(rel.data(), rc.maxrel, rel.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(need.data(), rc.colmask, need.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaStreamSynchronize(st));
+      double cur = 0;
+      for (size_t k = 0; k < rel.size(); ++k)
+        if (need[k]) cur = std::max(cur, rel[k]);
+      if (cur < 0.5 * best) { best = cur; stall = 0; }
+      else if (++stall >= o.stall_sweeps) break;
+      CBS_TRY(b32.replace(rc.R, rc.colmask, st));
+    }
+    CBS_CUDA(cudaMemcpyAsync(it_tmp.data(), b32.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), b32.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaStreamSynchronize(st));
+    for (size_t k = 0; k < iters.size(); ++k) {
+      iters[k] = it_tmp[k];
+      flags[k] |= (fl_tmp[k] & 2);
+    }
+    if (unconv > 0) {
+      // FP64 continuation for the columns left: BiCG on P(z) D = R, P(z)^dagger D~ = R~
+      // to tol relative to the original right-hand side, then Y += D
+      b32.release();
+      CBS_TRY(b64.alloc(H, n, L));
+      CBS_TRY(b64.set_systems(zs, Es, st));
+      CBS_TRY(b64.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
+                       rc.colmask, 0.5 * o.tol, 0.0, st, rc.bn2));
+      int done = 0;
+      CBS_TRY(b64.iterate(o.tol, o.max_iter, o.check_every, st, &done));
+      CBS_TRY(launch_accumulate((int64_t)2 * n * H.n * L, Y, b64.x, st));
+      CBS_TRY(rc.run(H, Y, B, b64.tw, b64.E, o.tol, st, &unconv));
+      CBS_CUDA(cudaMemcpyAsync(it_tmp.data(), b64.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), b64.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
       CBS_CUDA(cudaStreamSynchronize(st));
       for (size_t k = 0; k < iters.size(); ++k) {
         iters[k] += it_tmp[k];
-        flags[k] |= (fl_tmp[k] & 2);   // breakdown is sticky; max_iter in an inner solve is not
+        flags[k] |= (fl_tmp[k] & 2);
       }
-      ++sweeps;
+      fp64_continued = true;
     }
     std::vector<int> mask((size_t)n * L);
     CBS_CUDA(cudaMemcpyAsync(maxrel.data(), rc.maxrel, (size_t)n * L * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -274,7 +313,7 @@ static cbs_status check_opts(const cbs_options *opt, cbs_options *o) {
   if (!(o->tol > 0) || !(o->delta > 0) || !(o->rho_max > 0) || o->max_iter < 1 ||
       (o->precision != CBS_FP64 && o->precision != CBS_FP32_REFINE) ||
       (o->extraction != CBS_HANKEL && o->extraction != CBS_RR) || !(o->inner_tol > 0) ||
-      o->max_sweeps < 0) {
+      o->max_sweeps < 0 || o->inner_max_iter < 1 || o->stall_sweeps < 1) {
     set_error("invalid cbs_options");
     return CBS_EINVAL;
   }
@@ -461,7 +500,8 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
       R.st.max_iters = mx;
       R.st.sweeps = S.sweeps;
       R.st.max_solve_residual = mr;
-      R.st.flags = (fl & 3) | (m == n ? 4 : 0) | (hsmall[2 * ne + e] ? 8 : 0) | (hsmall[3 * ne + e] ? 16 : 0);
+      R.st.flags = (fl & 3) | (m == n ? 4 : 0) | (hsmall[2 * ne + e] ? 8 : 0) | (hsmall[3 * ne + e] ? 16 : 0) |
+                   (S.fp64_continued ? 32 : 0);
       if (fl & 2) ret = (ret == CBS_OK ? CBS_EBREAKDOWN : ret);
       else if (fl & 1) ret = (ret == CBS_OK ? CBS_ENOCONV : ret);
       else if (m == n && ret == CBS_OK) ret = CBS_WRANK;
