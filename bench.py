@@ -213,6 +213,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="c2")
+    ap.add_argument("--energies", type=int, default=0,
+                    help="solve only the first K energies of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
@@ -236,7 +238,7 @@ def main():
     dev = torch.device("cuda", local)
 
     wl = synth.workload(args.workload)
-    energies = wl.energies
+    energies = wl.energies if args.energies <= 0 else wl.energies[:args.energies]
     n_e = len(energies)
     H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
     Vd = torch.from_numpy(wl.V).to(dev).contiguous()

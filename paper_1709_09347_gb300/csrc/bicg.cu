@@ -394,6 +394,11 @@ void Bicg<R>::release() {
   block = nullptr;
   for (int k = 0; k < n_prof_ev; ++k) cudaEventDestroy(prof_ev[k]);
   n_prof_ev = 0;
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
+  exec_max_iter = exec_check_every = -1;
+  if (h_active) cudaFreeHost(h_active);
+  h_active = nullptr;
 }
 
 template <typename R>
@@ -469,32 +474,34 @@ cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStrea
     for (int k = 0; k < ne; ++k) CBS_CUDA(cudaEventCreate(&prof_ev[k]));
     n_prof_ev = ne;
   }
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  const uint64_t c0 = launches_so_far();
-  CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  cbs_status s = CBS_OK;
-  for (int k = 0; k < check_every && s == CBS_OK; ++k) s = step(tol, max_iter, st, k);
-  cudaError_t ce = cudaStreamEndCapture(st, &graph);
-  const uint64_t per_graph = launches_so_far() - c0;
-  uncount_launches(per_graph);
-  if (s != CBS_OK) { if (graph) cudaGraphDestroy(graph); return s; }
-  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-  ce = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-  int *h_active = nullptr;
-  ce = cudaMallocHost(&h_active, sizeof(int));
-  if (ce != cudaSuccess) { cudaGraphExecDestroy(exec); return cuda_fail(ce, "cudaMallocHost"); }
+  if (!h_active) CBS_CUDA(cudaMallocHost(&h_active, sizeof(int)));
+  if (!exec || exec_max_iter != max_iter || exec_check_every != check_every) {
+    if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    const uint64_t c0 = launches_so_far();
+    CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cbs_status s = CBS_OK;
+    for (int k = 0; k < check_every && s == CBS_OK; ++k) s = step(tol, max_iter, st, k);
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    exec_kernels = launches_so_far() - c0;
+    uncount_launches(exec_kernels);
+    if (s != CBS_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { exec = nullptr; return cuda_fail(ce, "cudaGraphInstantiate"); }
+    exec_max_iter = max_iter;
+    exec_check_every = check_every;
+  }
   int done = 0;
-  s = CBS_OK;
+  cbs_status s = CBS_OK;
   // every replay advances all still-active columns by check_every iterations; max_iter is
   // also enforced per column on the device, so the loop ends within max_iter/check_every + 1
   int max_replays = max_iter / check_every + 2;
   if (call_cap > 0) max_replays = std::min(max_replays, (call_cap + check_every - 1) / check_every);
   for (int rep = 0; rep < max_replays; ++rep) {
-    ce = cudaGraphLaunch(exec, st);
-    count_launches(per_graph);
+    cudaError_t ce = cudaGraphLaunch(exec, st);
+    count_launches(exec_kernels);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { s = cuda_fail(ce, "BiCG graph replay"); break; }
@@ -512,8 +519,6 @@ cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStrea
     done += check_every;
     if (*h_active == 0) break;
   }
-  cudaFreeHost(h_active);
-  cudaGraphExecDestroy(exec);
   if (host_iters_done) *host_iters_done = done;
   return s;
 }

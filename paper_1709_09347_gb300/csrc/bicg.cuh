@@ -35,6 +35,11 @@ struct Bicg {
   int n_prof_ev = 0;
   unsigned long long *sys_apply = nullptr;   // device: active systems summed over applies
   double prof_ms = 0, prof_launches = 0;
+  // the captured iteration graph is reused across iterate() calls with the same shape
+  cudaGraphExec_t exec = nullptr;
+  int exec_max_iter = -1, exec_check_every = -1;
+  uint64_t exec_kernels = 0;
+  int *h_active = nullptr;                   // pinned host word for the convergence poll
 
   static size_t bytes_needed(const HamView &H, int n, int L);
   cbs_status alloc(const HamView &H, int n, int L);

@@ -134,6 +134,7 @@ struct ResidualCheck {
   }
   // Y: [2n][N][L]; tw/E: twists [2n] and energies [2n]
   bool profile = false;
+  bool have_bn = false;
   double prof_ms = 0, prof_launches = 0, prof_outputs = 0;
   cbs_status run(const HamView &H, const double2 *Y, const double2 *B, const double2 *tw,
                  const double *E, double tol, cudaStream_t st, int *host_unconv) {
@@ -156,9 +157,12 @@ struct ResidualCheck {
       cudaEventDestroy(e1);
     }
     CBS_TRY(launch_residual(2 * n, N, L, B, 0, B, 0, n, R, cn, st));
-    k_col_norms<<<1, L, 0, st>>>(N, L, B, bn); cbs::count_launches(1);
-    k_bnorm_expand<<<2 * n, L, 0, st>>>(2 * n, L, bn, bn2); cbs::count_launches(1);
-    CBS_CUDA(cudaGetLastError());
+    if (!have_bn) {   // the right-hand sides do not change between calls
+      k_col_norms<<<1, L, 0, st>>>(N, L, B, bn); cbs::count_launches(1);
+      k_bnorm_expand<<<2 * n, L, 0, st>>>(2 * n, L, bn, bn2); cbs::count_launches(1);
+      CBS_CUDA(cudaGetLastError());
+      have_bn = true;
+    }
     CBS_CUDA(cudaMemsetAsync(nunc, 0, sizeof(int), st));
     CBS_TRY(launch_refine_check(n, L, 64, cn, bn2, tol, colmask, nunc, maxrel, st));
     if (host_unconv) {
@@ -187,17 +191,21 @@ struct ShiftedSolver {
   cbs_status collect_profile(cudaStream_t st) {
     double o64 = 0, o32 = 0;
     if (b64.block && b64.profile) CBS_TRY(b64.prof_outputs(st, &o64));
-    if (b32.block && b32.profile) CBS_TRY(b32.prof_outputs(st, &o32));
+    if (b32.block && b32.profile) {
+      CBS_TRY(b32.prof_outputs(st, &o32));
+      prof32_ms = b32.prof_ms;
+      prof32_launches = b32.prof_launches;
+      prof32_outputs = o32;
+    }
     prof_ms[CBS_C128] = b64.prof_ms + rc.prof_ms;
     prof_launches[CBS_C128] = b64.prof_launches + rc.prof_launches;
     prof_outputs[CBS_C128] = o64 + rc.prof_outputs;
-    prof_ms[CBS_C64] = b32.prof_ms;
-    prof_launches[CBS_C64] = b32.prof_launches;
-    prof_outputs[CBS_C64] = o32;
+    prof_ms[CBS_C64] = prof32_ms;
+    prof_launches[CBS_C64] = prof32_launches;
+    prof_outputs[CBS_C64] = prof32_outputs;
     return CBS_OK;
   }
-
-  ~ShiftedSolver() { b64.release(); b32.release(); }
+  double prof32_ms = 0, prof32_launches = 0, prof32_outputs = 0;
 
   static size_t bytes_per_system(const HamView &H, int L, int precision) {
     const size_t v16 = (size_t)H.n * L * 16;
@@ -246,10 +254,8 @@ struct ShiftedSolver {
     CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));   // R = B
     CBS_TRY(b32.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
                      rc.colmask, 0.25 * o.tol, o.inner_tol, st));
-    std::vector<double> rel((size_t)n * L);
-    std::vector<int> need((size_t)n * L);
-    double best = 1e300;
-    int stall = 0;
+    std::vector<double> rel((size_t)n * L), best((size_t)n * L, 1e300);
+    std::vector<int> need((size_t)n * L), stall((size_t)n * L, 0);
     for (int sw = 0; sw < o.max_sweeps && unconv > 0; ++sw) {
       int done = 0;
       CBS_TRY(b32.iterate(o.tol, o.max_iter, o.check_every, st, &done, o.inner_max_iter));
@@ -257,16 +263,22 @@ struct ShiftedSolver {
       CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));
       ++sweeps;
       if (unconv == 0) break;
-      // stagnation of the FP64 true residual: the single-precision recursion no longer
-      // makes progress on the columns that are left (loss of bi-orthogonality)
+      // per column: stagnation of the FP64 true residual means the single-precision
+      // recursion no longer makes progress there (loss of bi-orthogonality); such columns
+      // leave the complex64 phases and are finished in FP64 below
       CBS_CUDA(cudaMemcpyAsync(rel.data(), rc.maxrel, rel.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
       CBS_CUDA(cudaMemcpyAsync(need.data(), rc.colmask, need.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
       CBS_CUDA(cudaStreamSynchronize(st));
-      double cur = 0;
-      for (size_t k = 0; k < rel.size(); ++k)
-        if (need[k]) cur = std::max(cur, rel[k]);
-      if (cur < 0.5 * best) { best = cur; stall = 0; }
-      else if (++stall >= o.stall_sweeps) break;
+      int live = 0;
+      for (size_t k = 0; k < rel.size(); ++k) {
+        if (!need[k]) continue;
+        if (rel[k] < 0.5 * best[k]) { best[k] = rel[k]; stall[k] = 0; }
+        else ++stall[k];
+        if (stall[k] >= o.stall_sweeps) need[k] = 0;
+        live += need[k];
+      }
+      if (live == 0) break;
+      CBS_CUDA(cudaMemcpyAsync(rc.colmask, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice, st));
       CBS_TRY(b32.replace(rc.R, rc.colmask, st));
     }
     CBS_CUDA(cudaMemcpyAsync(it_tmp.data(), b32.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -276,6 +288,8 @@ struct ShiftedSolver {
       iters[k] = it_tmp[k];
       flags[k] |= (fl_tmp[k] & 2);
     }
+    CBS_TRY(collect_profile(st));
+    if (unconv > 0) CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));   // full mask
     if (unconv > 0) {
       // FP64 continuation for the columns left: BiCG on P(z) D = R, P(z)^dagger D~ = R~
       // to tol relative to the original right-hand side, then Y += D
