@@ -216,6 +216,11 @@ def main():
     ap.add_argument("--energies", type=int, default=0,
                     help="solve only the first K energies of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spmm", action="store_true",
+                    help="only time the operator apply (stencil + projector SpMM) and exit")
+    ap.add_argument("--spmm-systems", type=int, default=0,
+                    help="systems per SpMM launch (default: all primal and dual systems of a step)")
+    ap.add_argument("--spmm-dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fp64-warmup", type=int, default=1)
@@ -242,6 +247,39 @@ def main():
     n_e = len(energies)
     H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
     Vd = torch.from_numpy(wl.V).to(dev).contiguous()
+
+    def spmm(n_sys, dtype_name, iters=20):
+        """Operator apply alone, at the batch shape of a step, timed with CUDA events on
+        torch's current stream (the stream the kernels are launched on)."""
+        dt = torch.complex64 if dtype_name == "c64" else torch.complex128
+        s = 8 if dtype_name == "c64" else 16
+        rng = np.random.default_rng(3)
+        zs = (np.exp(1j * rng.uniform(0, 2 * np.pi, n_sys)) *
+              np.where(np.arange(n_sys) % 2 == 0, 1 / wl.lambda_min, wl.lambda_min))
+        plan = cbs.ApplyPlan(H, zs, 0.1, wl.L, dt)
+        X = torch.randn(n_sys, wl.grid.n, wl.L, dtype=dt, device=dev)
+        Yo = torch.empty_like(X)
+        for _ in range(3):
+            plan(X, Yo)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(iters):
+            plan(X, Yo)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / iters
+        outputs = n_sys * wl.grid.n * wl.L
+        bpo = bytes_per_output(wl, s)
+        hbm, src = _peaks()
+        r = {"dtype": dtype_name, "systems": n_sys, "columns": wl.L, "ms_per_launch": ms,
+             "bytes_per_launch": bpo * outputs, "GB_s": bpo * outputs / (ms / 1e3) / 1e9,
+             "peak_GB_s": hbm, "peak_source": src,
+             "frac": bpo * outputs / (ms / 1e3) / 1e9 / hbm,
+             "TFLOP_s": flops_per_output(wl) * outputs / (ms / 1e3) / 1e12}
+        del X, Yo, plan
+        torch.cuda.empty_cache()
+        return r
 
     def barrier():
         if world > 1:
@@ -279,6 +317,12 @@ def main():
 
     hbm, hbm_src = _peaks()
     sha = _apply_sha()
+    n_step_sys = 2 * wl.n_int * n_e
+    if args.spmm:
+        r = spmm(args.spmm_systems or n_step_sys, args.spmm_dtype)
+        if rank == 0:
+            print(json.dumps({"spmm": r, "workload": args.workload}), flush=True)
+        return
 
     def roofline_for(results, precision, ms_total):
         key = "c64" if precision == "fp32_refine" else "c128"
@@ -360,6 +404,8 @@ def main():
     e2e = {"value": e2e_steps * n_e * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
 
+    spmm_res = {"c64": spmm(n_step_sys, "c64"), "c128": spmm(n_step_sys, "c128", iters=3)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -381,7 +427,7 @@ def main():
                        "energies_per_step": n_e, "l2": "state per step >> L2 (no flush needed)",
                        "kept_per_energy": kept, "max_residual": worst_res, "flags": flags},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
-            "cpu_baseline": cpu, "fp64": fp64,
+            "cpu_baseline": cpu, "fp64": fp64, "spmm": spmm_res,
             "stage_ms_last_step": {"solve": last.ms_solve, "moments": last.ms_moments,
                                    "extract": last.ms_extract},
         }

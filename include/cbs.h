@@ -137,6 +137,17 @@ cbs_status cbs_hamiltonian_norms(const cbs_hamiltonian *h, double E, double *n_p
 cbs_status cbs_apply(const cbs_hamiltonian *h, int n_sys, const double *z, const double *E,
                      int L, const void *X, void *Y, int dtype, void *stream);
 
+/* Bytes of device workspace cbs_apply_ws needs for n_sys systems of L columns. */
+size_t cbs_apply_workspace_size(const cbs_hamiltonian *h, int n_sys, int L, int dtype);
+
+/* As cbs_apply, with all pointers on the device and caller-provided workspace, so that
+ * the call allocates nothing, does not synchronise and can be captured in a CUDA graph:
+ * z: DEVICE complex128 [n_sys]; E: DEVICE double [n_sys]; workspace: DEVICE buffer of at
+ * least cbs_apply_workspace_size bytes (16-byte aligned), overwritten by the call. */
+cbs_status cbs_apply_ws(const cbs_hamiltonian *h, int n_sys, const double *z, const double *E,
+                        int L, const void *X, void *Y, int dtype, void *workspace,
+                        size_t workspace_bytes, void *stream);
+
 /* Shifted solves of §3.2 for a batch of n_sys points: BiCG on P(z_s) Y[s] = B and, as
  * its dual, P(z_s)^dagger Yd[s] = B (= P(1/conj z_s) Yd[s] = B).
  * z, E: host arrays [n_sys]; B: DEVICE [N][L] complex128 (shared by all systems);

@@ -27,7 +27,7 @@ EXPORTS = (
     "cbs_hamiltonian_norms", "cbs_apply", "cbs_solve_shifted", "cbs_solve", "cbs_result_count",
     "cbs_result_get", "cbs_result_stats", "cbs_result_all", "cbs_result_moments", "cbs_result_iters",
     "cbs_result_timing", "cbs_result_profile", "cbs_result_free", "cbs_last_error",
-    "cbs_kernel_launches",
+    "cbs_kernel_launches", "cbs_apply_workspace_size", "cbs_apply_ws",
 )
 
 
@@ -102,6 +102,9 @@ def load():
     lib.cbs_result_free.argtypes = [V]
     lib.cbs_result_free.restype = None
     lib.cbs_last_error.restype = ct.c_char_p
+    lib.cbs_apply_workspace_size.argtypes = [V, I, I, I]
+    lib.cbs_apply_workspace_size.restype = ct.c_size_t
+    lib.cbs_apply_ws.argtypes = [V, I, V, V, I, V, V, I, V, ct.c_size_t, V]
     lib.cbs_kernel_launches.argtypes = []
     lib.cbs_kernel_launches.restype = ct.c_uint64
     _lib = lib
@@ -287,3 +290,30 @@ def solve(H: Hamiltonian, energies, lambda_min, n_int, L, M, V, opts: Options | 
 def kernel_launches() -> int:
     """Kernels launched by libcbs in this process so far (graph replays count every node)."""
     return int(load().cbs_kernel_launches())
+
+
+class ApplyPlan:
+    """Preallocated operator apply (cbs_apply_ws): device twists, energies and workspace
+    held by torch tensors; each call launches on torch's current stream, allocates
+    nothing and does not synchronise."""
+
+    def __init__(self, H: Hamiltonian, z, E, L: int, dtype):
+        import torch
+        self.H, self.L = H, int(L)
+        z = np.atleast_1d(np.asarray(z, complex))
+        self.n_sys = len(z)
+        E = np.ascontiguousarray(np.broadcast_to(np.asarray(E, float), (self.n_sys,)))
+        self.dt = {torch.complex128: CBS_C128, torch.complex64: CBS_C64}[dtype]
+        self.z = torch.from_numpy(np.ascontiguousarray(z)).to("cuda")
+        self.E = torch.from_numpy(E).to("cuda")
+        nbytes = int(load().cbs_apply_workspace_size(H.handle, self.n_sys, self.L, self.dt))
+        self.ws = torch.empty(max(nbytes, 16), dtype=torch.uint8, device="cuda")
+
+    def __call__(self, X, Y):
+        import torch
+        assert X.is_cuda and Y.is_cuda and X.is_contiguous() and Y.is_contiguous()
+        _check(load().cbs_apply_ws(self.H.handle, self.n_sys, ct.c_void_p(self.z.data_ptr()),
+                                   ct.c_void_p(self.E.data_ptr()), self.L, ct.c_void_p(X.data_ptr()),
+                                   ct.c_void_p(Y.data_ptr()), self.dt, ct.c_void_p(self.ws.data_ptr()),
+                                   self.ws.numel(), _stream_ptr(torch)))
+        return Y

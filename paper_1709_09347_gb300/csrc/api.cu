@@ -60,7 +60,7 @@ extern "C" cbs_status cbs_apply(const cbs_hamiltonian *h, int n_sys, const doubl
   cudaStream_t st = (cudaStream_t)stream;
   const HamView &H = h->v;
   const size_t csz = dtype == CBS_C128 ? sizeof(double2) : sizeof(float2);
-  const size_t dbytes = (size_t)n_sys * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * csz;
+  const size_t dbytes = (size_t)n_sys * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * csz;
   void *scratch = nullptr;
   const size_t sys_bytes = (size_t)n_sys * (sizeof(double2) + sizeof(double));
   CBS_CUDA(cudaMalloc(&scratch, dbytes + sys_bytes + 256));
@@ -84,4 +84,32 @@ extern "C" cbs_status cbs_apply(const cbs_hamiltonian *h, int n_sys, const doubl
   cudaFree(scratch);
   if (s == CBS_OK && e2 != cudaSuccess) s = cuda_fail(e2, "cbs_apply");
   return s;
+}
+
+extern "C" size_t cbs_apply_workspace_size(const cbs_hamiltonian *h, int n_sys, int L, int dtype) {
+  if (!h || n_sys < 1 || L < 1) return 0;
+  const HamView &H = h->v;
+  const size_t csz = dtype == CBS_C128 ? sizeof(double2) : sizeof(float2);
+  return (size_t)n_sys * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * csz;
+}
+
+extern "C" cbs_status cbs_apply_ws(const cbs_hamiltonian *h, int n_sys, const double *z, const double *E,
+                                   int L, const void *X, void *Y, int dtype, void *workspace,
+                                   size_t workspace_bytes, void *stream) {
+  if (!h || !z || !E || !X || !Y || !workspace || n_sys < 1 || L < 1 || L > 1024) {
+    set_error("cbs_apply_ws: bad argument (need n_sys >= 1, 1 <= L <= 1024, non-null pointers)");
+    return CBS_EINVAL;
+  }
+  if (dtype != CBS_C128 && dtype != CBS_C64) { set_error("cbs_apply_ws: dtype"); return CBS_EINVAL; }
+  if (workspace_bytes < cbs_apply_workspace_size(h, n_sys, L, dtype)) {
+    set_error("cbs_apply_ws: workspace smaller than cbs_apply_workspace_size");
+    return CBS_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const HamView &H = h->v;
+  if (dtype == CBS_C128)
+    return apply_P<double>(H, n_sys, L, (const double2 *)X, (double2 *)Y, (const double2 *)z, false, E,
+                           (double2 *)workspace, nullptr, st);
+  return apply_P<float>(H, n_sys, L, (const float2 *)X, (float2 *)Y, (const double2 *)z, false, E,
+                        (float2 *)workspace, nullptr, st);
 }

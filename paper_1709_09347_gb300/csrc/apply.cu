@@ -18,6 +18,11 @@
 
 namespace cbs {
 
+__device__ __forceinline__ float4 c2mul(float2 w0, float2 w1, float4 v) {
+  const float2 a = cmul(w0, make_float2(v.x, v.y)), b = cmul(w1, make_float2(v.z, v.w));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
 template <typename R> __device__ __forceinline__ const R *vloc_ptr(const HamView &H);
 template <> __device__ __forceinline__ const double *vloc_ptr<double>(const HamView &H) { return H.vloc; }
 template <> __device__ __forceinline__ const float *vloc_ptr<float>(const HamView &H) { return H.vloc32; }
@@ -96,7 +101,89 @@ __global__ void k_proj_gather(HamView H, int L, const typename CT<R>::T *__restr
         d.x += hv * cc[nu].x;
         d.y += hv * cc[nu].y;
       }
-      D[(((int64_t)s * H.n_atoms + a) * np + mu) * L + c] = d;
+      D[(((int64_t)s * H.n_atoms + a) * L + c) * H.np4 + mu] = d;
+    }
+    for (int mu = np; mu < H.np4; ++mu) D[(((int64_t)s * H.n_atoms + a) * L + c) * H.np4 + mu] = mk<R>(0, 0);
+  }
+}
+
+// Complex64 gather with two columns per thread (16-byte loads):
+// D[s][a][c][4] = h_a sum_{t in a} p_t w^{-m_t} X[s][i_t][c], for n_proj <= 4.
+template <bool PER_COL>
+__global__ void k_proj_gather_c64x2(HamView H, int L, const float4 *__restrict__ X,
+                                    const double2 *__restrict__ twist, float2 *__restrict__ D,
+                                    const int *__restrict__ sys_active) {
+  extern __shared__ float4 red4[];   // [py][4 projectors][L/2] pairs of complex
+  const int a = blockIdx.x, s = blockIdx.y;
+  const int t = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
+  const int L2 = L >> 1;
+  if (sys_active && !sys_active[s]) return;
+  const double2 wd0 = twist[PER_COL ? (int64_t)s * L + 2 * t : s];
+  const double2 wd1 = twist[PER_COL ? (int64_t)s * L + 2 * t + 1 : s];
+  const float2 w0 = from_d<float>(wd0), w1 = from_d<float>(wd1);
+  const float2 wi0 = from_d<float>(cdiv(make_double2(1.0, 0.0), wd0));
+  const float2 wi1 = from_d<float>(cdiv(make_double2(1.0, 0.0), wd1));
+  float4 acc[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) acc[mu] = make_float4(0, 0, 0, 0);
+  const int np = H.n_proj;
+  const float *pv = H.sup_val32;
+  const int64_t t0 = H.sup_ptr[a], t1 = H.sup_ptr[a + 1];
+  const float4 *Xs = X + (int64_t)s * H.n * L2;
+  constexpr int U = 4;
+  for (int64_t tb = t0 + ly; tb < t1; tb += (int64_t)U * py) {
+    float4 xv[U];
+    int mw[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tt = tb + (int64_t)u * py;
+      if (tt < t1) {
+        xv[u] = Xs[(int64_t)H.sup_idx[tt] * L2 + t];
+        mw[u] = H.sup_wrap[tt];
+      } else {
+        xv[u] = make_float4(0, 0, 0, 0);
+        mw[u] = 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tt = tb + (int64_t)u * py;
+      if (tt >= t1) break;
+      float4 f = xv[u];
+      if (mw[u] > 0) f = c2mul(wi0, wi1, f);       // w^{-m} x
+      else if (mw[u] < 0) f = c2mul(w0, w1, f);
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu)
+        if (mu < np) {
+          const float p = pv[tt * np + mu];
+          acc[mu].x += p * f.x; acc[mu].y += p * f.y; acc[mu].z += p * f.z; acc[mu].w += p * f.w;
+        }
+    }
+  }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) red4[((int64_t)ly * 4 + mu) * L2 + t] = acc[mu];
+  __syncthreads();
+  if (ly == 0) {
+    float4 cc[4];
+    for (int mu = 0; mu < 4; ++mu) {
+      float4 sum = make_float4(0, 0, 0, 0);
+      for (int y = 0; y < py; ++y) {
+        const float4 v = red4[((int64_t)y * 4 + mu) * L2 + t];
+        sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+      }
+      cc[mu] = sum;
+    }
+    const float *ha = H.h32 + (int64_t)a * np * np;
+    float2 *Da = D + (((int64_t)s * H.n_atoms + a) * L + 2 * t) * 4;   // columns 2t, 2t+1
+    for (int mu = 0; mu < 4; ++mu) {
+      float4 d = make_float4(0, 0, 0, 0);
+      if (mu < np)
+        for (int nu = 0; nu < np; ++nu) {
+          const float hv = ha[mu * np + nu];
+          d.x += hv * cc[nu].x; d.y += hv * cc[nu].y; d.z += hv * cc[nu].z; d.w += hv * cc[nu].w;
+        }
+      Da[mu] = make_float2(d.x, d.y);
+      Da[4 + mu] = make_float2(d.z, d.w);
     }
   }
 }
@@ -180,11 +267,11 @@ __global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typena
     if (D) {
       for (int qq = e0; qq < e1; ++qq) {
         const int t = H.pt_ent[qq], a = H.pt_atom[qq];
-        const C *Da = D + (((int64_t)s * H.n_atoms + a) * np) * L + c;
+        const C *Da = D + (((int64_t)s * H.n_atoms + a) * L + c) * H.np4;
         C v = mk<R>(0, 0);
         for (int mu = 0; mu < np; ++mu) {
           const R p = pv[t * np + mu];
-          const C dv = Da[mu * L];
+          const C dv = Da[mu];
           v.x += p * dv.x;
           v.y += p * dv.y;
         }
@@ -194,6 +281,91 @@ __global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typena
       }
     }
     Ys[b] = mk<R>(e * x0.x - acc.x, e * x0.y - acc.y);
+#pragma unroll
+    for (int d = 0; d < 2 * MH; ++d) q[d] = q[d + 1];
+  }
+}
+
+// Complex64 fast path: each thread owns two adjacent columns of one (x, y) line, so every
+// load and store is 16 bytes; z arms from the register queue of Bloch-extended values;
+// the projector scatter reads one packed (atom, wrap) word, one float4 of projector values
+// and 64 bytes of D per covering entry (D laid out [system][atom][column][4]).
+
+template <bool PER_COL, int MH>
+__global__ void __launch_bounds__(256, 3) k_apply_c64x2(HamView H, int L, const float4 *__restrict__ X,
+                                                        float4 *__restrict__ Y,
+                                                        const double2 *__restrict__ twist,
+                                                        const double *__restrict__ E,
+                                                        const float4 *__restrict__ D,
+                                                        const int *__restrict__ sys_active) {
+  const int s = blockIdx.z;
+  if (sys_active && !sys_active[s]) return;
+  const int t = threadIdx.x;                 // column pair
+  const int L2 = L >> 1;
+  const int ix = blockIdx.x * blockDim.y + threadIdx.y;
+  const int iy = blockIdx.y;
+  if (ix >= H.nx) return;
+  const int nx = H.nx, ny = H.ny, nz = H.nz, nxy = nx * ny;
+  const double2 wd0 = twist[PER_COL ? (int64_t)s * L + 2 * t : s];
+  const double2 wd1 = twist[PER_COL ? (int64_t)s * L + 2 * t + 1 : s];
+  const double2 wid0 = cdiv(make_double2(1.0, 0.0), wd0), wid1 = cdiv(make_double2(1.0, 0.0), wd1);
+  const float2 w0 = from_d<float>(wd0), w1 = from_d<float>(wd1);
+  const float2 wi0 = from_d<float>(wid0), wi1 = from_d<float>(wid1);
+  const float e = (float)E[s];
+  const float dk = H.diag_kin32;
+  // neighbour offsets in float4 units (x and y periodic); recomputed, not kept in registers
+  auto oxp = [&](int k) { return (ix + k < nx ? k : k - nx) * L2; };
+  auto oxm = [&](int k) { return (ix - k >= 0 ? -k : nx - k) * L2; };
+  auto oyp = [&](int k) { return (iy + k < ny ? k : k - ny) * nx * L2; };
+  auto oym = [&](int k) { return (iy - k >= 0 ? -k : ny - k) * nx * L2; };
+  const float *vl = H.vloc32;
+  const float4 *Xs = X + (int64_t)s * H.n * L2;
+  float4 *Ys = Y + (int64_t)s * H.n * L2;
+  const float4 *Ds = D + (int64_t)s * H.n_atoms * L * 2 + 4 * t;   // column pair 2t, 2t+1
+  const int line = iy * nx + ix;
+  auto bloch = [&](int p) -> float4 {
+    if (p >= nz) return c2mul(w0, w1, Xs[((p - nz) * nxy + line) * L2 + t]);
+    if (p < 0) return c2mul(wi0, wi1, Xs[((p + nz) * nxy + line) * L2 + t]);
+    return Xs[(p * nxy + line) * L2 + t];
+  };
+  float4 q[2 * MH + 1];
+#pragma unroll
+  for (int d = 0; d < 2 * MH; ++d) q[d] = bloch(d - MH);
+  for (int iz = 0; iz < nz; ++iz) {
+    const int pt = iz * nxy + line;
+    int e0 = 0, e1 = 0;
+    if (D) { e0 = (int)H.pt_ptr[pt]; e1 = (int)H.pt_ptr[pt + 1]; }
+    q[2 * MH] = bloch(iz + MH);
+    const int b = pt * L2 + t;
+    const float4 x0 = q[MH];
+    const float dd = dk + vl[pt];
+    float4 acc = make_float4(dd * x0.x, dd * x0.y, dd * x0.z, dd * x0.w);
+#pragma unroll
+    for (int k = 1; k <= MH; ++k) {
+      const float4 a1 = Xs[b + oxp(k)], a2 = Xs[b + oxm(k)];
+      const float4 b1 = Xs[b + oyp(k)], b2 = Xs[b + oym(k)];
+      const float4 z1 = q[MH + k], z2 = q[MH - k];
+      const float wx = H.w32[0][k], wy = H.w32[1][k], wz = H.w32[2][k];
+      acc.x += wx * (a1.x + a2.x) + wy * (b1.x + b2.x) + wz * (z1.x + z2.x);
+      acc.y += wx * (a1.y + a2.y) + wy * (b1.y + b2.y) + wz * (z1.y + z2.y);
+      acc.z += wx * (a1.z + a2.z) + wy * (b1.z + b2.z) + wz * (z1.z + z2.z);
+      acc.w += wx * (a1.w + a2.w) + wy * (b1.w + b2.w) + wz * (z1.w + z2.w);
+    }
+    for (int qq = e0; qq < e1; ++qq) {
+      const int2 aw = H.pt_aw[qq];
+      const float4 p = H.pt_p32[qq];
+      const float4 *Da = Ds + (int64_t)aw.x * L * 2;
+      const float4 d0 = Da[0], d1 = Da[1], d2 = Da[2], d3 = Da[3];
+      float4 v;
+      v.x = p.x * d0.x + p.y * d0.z + p.z * d1.x + p.w * d1.z;
+      v.y = p.x * d0.y + p.y * d0.w + p.z * d1.y + p.w * d1.w;
+      v.z = p.x * d2.x + p.y * d2.z + p.z * d3.x + p.w * d3.z;
+      v.w = p.x * d2.y + p.y * d2.w + p.z * d3.y + p.w * d3.w;
+      if (aw.y > 0) v = c2mul(w0, w1, v);            // w^{m} v
+      else if (aw.y < 0) v = c2mul(wi0, wi1, v);
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    Ys[b] = make_float4(e * x0.x - acc.x, e * x0.y - acc.y, e * x0.z - acc.z, e * x0.w - acc.w);
 #pragma unroll
     for (int d = 0; d < 2 * MH; ++d) q[d] = q[d + 1];
   }
@@ -210,6 +382,20 @@ cbs_status launch_proj_gather(const HamView &H, int n_sys, int L, const typename
   if (sm > 48 * 1024) {
     set_error("projector gather: shared memory per block exceeds 48 KB (reduce L)");
     return CBS_EINVAL;
+  }
+  if (sizeof(typename CT<R>::T) == sizeof(float2) && L % 2 == 0 && L <= 512 && H.np4 == 4) {
+    const int L2 = L / 2;
+    int py = 256 / L2;
+    if (py < 1) py = 1;
+    dim3 b2((unsigned)L2, (unsigned)py, 1);
+    const size_t sm2 = (size_t)py * 4 * L2 * sizeof(float4);
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    float2 *D2 = reinterpret_cast<float2 *>(D);
+    if (per_col) k_proj_gather_c64x2<true><<<grd, b2, sm2, st>>>(H, L, X4, twist, D2, sys_active);
+    else k_proj_gather_c64x2<false><<<grd, b2, sm2, st>>>(H, L, X4, twist, D2, sys_active);
+    cbs::count_launches(1);
+    CBS_CUDA(cudaGetLastError());
+    return CBS_OK;
   }
   if (per_col)
     k_proj_gather<R, true><<<grd, blk, sm, st>>>(H, L, X, twist, D, sys_active);
@@ -229,9 +415,38 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
     set_error("apply: N*L must be below 2^31");
     return CBS_EINVAL;
   }
+  const typename CT<R>::T *Dp = H.n_atoms ? D : nullptr;
+  // complex64 with an even number of columns and at most 4 projectors: two columns per thread
+  if (sizeof(typename CT<R>::T) == sizeof(float2) && L % 2 == 0 && L <= 512 && H.np4 == 4) {
+    const int L2 = L / 2;
+    int py = 256 / L2;
+    if (py < 1) py = 1;
+    dim3 blk((unsigned)L2, (unsigned)py, 1);
+    dim3 grd((unsigned)ceil_div(H.nx, py), (unsigned)H.ny, (unsigned)n_sys);
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    float4 *Y4 = reinterpret_cast<float4 *>(Y);
+    const float4 *D4 = H.n_atoms ? reinterpret_cast<const float4 *>(D) : nullptr;
+#define FX(MH)                                                                                     \
+  do {                                                                                             \
+    if (per_col) k_apply_c64x2<true, MH><<<grd, blk, 0, st>>>(H, L, X4, Y4, twist, E, D4, sys_active); \
+    else k_apply_c64x2<false, MH><<<grd, blk, 0, st>>>(H, L, X4, Y4, twist, E, D4, sys_active);    \
+    cbs::count_launches(1);                                                                        \
+  } while (0)
+    switch (H.m) {
+      case 1: FX(1); break;
+      case 2: FX(2); break;
+      case 3: FX(3); break;
+      case 4: FX(4); break;
+      case 5: FX(5); break;
+      case 6: FX(6); break;
+      default: set_error("apply: FD half-width must be 1..6"); return CBS_EINVAL;
+    }
+#undef FX
+    CBS_CUDA(cudaGetLastError());
+    return CBS_OK;
+  }
   dim3 blk = col_block(L);
   dim3 grd((unsigned)ceil_div(H.nx, blk.y), (unsigned)H.ny, (unsigned)n_sys);
-  const typename CT<R>::T *Dp = H.n_atoms ? D : nullptr;
 #define ZM(MH)                                                                                  \
   do {                                                                                          \
     if (per_col) k_apply_zm<R, true, MH><<<grd, blk, 0, st>>>(H, L, X, Y, twist, E, Dp, sys_active); \

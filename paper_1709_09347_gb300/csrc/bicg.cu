@@ -341,7 +341,7 @@ size_t Bicg<R>::bytes_needed(const HamView &H, int n, int L) {
   chunking(H.n, L, &cp, &nc);
   const int64_t vec = (int64_t)2 * n * H.n * L * sizeof(C);
   int64_t b = 4 * align256(vec);
-  b += align256((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * sizeof(C));
+  b += align256((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * sizeof(C));
   b += align256((int64_t)2 * n * sizeof(double2)) + align256((int64_t)2 * n * sizeof(double));
   b += 4 * align256((int64_t)n * L * sizeof(double2)) + 6 * align256((int64_t)n * L * sizeof(double));
   b += 3 * align256((int64_t)n * L * sizeof(int)) + align256((int64_t)2 * n * sizeof(int)) + 256;
@@ -364,7 +364,7 @@ cbs_status Bicg<R>::alloc(const HamView &H_, int n_, int L_) {
   auto take = [&](int64_t sz) { char *r = b; b += align256(sz); return (void *)r; };
   const int64_t vec = (int64_t)2 * n * N * L * sizeof(C);
   x = (C *)take(vec); r = (C *)take(vec); p = (C *)take(vec); q = (C *)take(vec);
-  D = (C *)take((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * sizeof(C));
+  D = (C *)take((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * sizeof(C));
   tw = (double2 *)take((int64_t)2 * n * sizeof(double2));
   E = (double *)take((int64_t)2 * n * sizeof(double));
   rho = (double2 *)take((int64_t)n * L * sizeof(double2));

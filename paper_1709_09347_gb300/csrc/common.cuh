@@ -81,6 +81,8 @@ struct HamView {
   int64_t n;                // nx*ny*nz
   double diag_kin;          // -1/2 c0 (1/hx^2 + 1/hy^2 + 1/hz^2)
   double wx[kMaxHalf + 1], wy[kMaxHalf + 1], wz[kMaxHalf + 1];  // -1/2 c_k / h^2 (k >= 1)
+  float w32[3][kMaxHalf + 1];   // the same weights in single precision (x, y, z)
+  float diag_kin32;
   const double *vloc;
   const float *vloc32;
   // projector table and its transpose (grid point -> covering entries)
@@ -95,6 +97,9 @@ struct HamView {
   const int64_t *pt_ptr;    // [n+1]
   const int32_t *pt_ent;    // [nnz] support entry index
   const int32_t *pt_atom;   // [nnz] atom of that entry
+  int np4;                  // projector slots per entry in D and pt_p32: 4 (n_proj <= 4) or 8
+  const int2 *pt_aw;        // [nnz] (atom, wrap) of each covering entry, point order
+  const float4 *pt_p32;     // [nnz] projector values of the entry, zero-padded to 4 (n_proj <= 4)
 };
 
 }  // namespace cbs
@@ -108,7 +113,7 @@ struct cbs_hamiltonian {
   // Frobenius pieces: ||H+||^2, ||H-||^2, off-diagonal part of ||H0||^2, sum d_i, sum d_i^2
   double fro_p2, fro_m2, fro_off0, diag_sum, diag_sum2;
   // device allocations owned by the handle
-  void *allocs[16];
+  void *allocs[24];
   int n_allocs;
 };
 
@@ -151,7 +156,7 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
                         typename CT<R>::T *Y, const double2 *twist, bool per_col,
                         const double *E, const typename CT<R>::T *D, const int *sys_active,
                         cudaStream_t st);
-// Y = P(w) X for n_sys systems; D is scratch of n_sys*n_atoms*n_proj*L elements
+// Y = P(w) X for n_sys systems; D is scratch of n_sys*n_atoms*np4*L elements
 template <typename R>
 cbs_status apply_P(const HamView &H, int n_sys, int L, const typename CT<R>::T *X,
                    typename CT<R>::T *Y, const double2 *twist, bool per_col, const double *E,

@@ -11,6 +11,8 @@
 // back-transform and S C) use a tiled complex FP64 GEMM.
 #include <math.h>
 
+#include <vector>
+
 #include "kernels.cuh"
 
 namespace cbs {
@@ -61,90 +63,99 @@ __global__ void k_hankel(int n_e, int L, int M, const double2 *mu, double2 *T, d
 
 // ------------------------------------------------------------------ Jacobi SVD
 // One-sided (Hestenes) Jacobi on the columns of A (n x n, column-major), accumulating
-// the right rotations in W.  Pairs are scheduled round-robin (n/2 disjoint pairs per
-// round), one warp per pair.  On exit sigma (descending), U = A/sigma and W sorted.
-constexpr int kSvdThreads = 1024;
-__global__ void __launch_bounds__(kSvdThreads) k_svd(int n, double2 *Ab, double2 *Wb, double2 *Ub,
-                                                     double2 *Wsb, double *sigb, int *info,
-                                                     double tolj, int max_sweeps) {
+// the right rotations in W.  A sweep is n2-1 rounds of n2/2 disjoint column pairs
+// (round-robin, n2 = n rounded up to even); each round is one launch in which every warp
+// of the grid handles one pair of one energy, so a round of all energies spreads over
+// the whole GPU (FP64 throughput per SM is small on GB300).  A sweep is captured once
+// as a CUDA graph and replayed until no pair of any energy needed a rotation.
+// On exit sigma (descending), U = A/sigma and W sorted accordingly.
+constexpr int kSvdThreads = 256;
+
+__global__ void k_svd_init(int n, double2 *Wb) {
+  const int e = blockIdx.y;
+  const int64_t nn = (int64_t)n * n;
+  double2 *W = Wb + e * nn;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nn;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    W[idx] = make_double2((idx % n) == (idx / n) ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void __launch_bounds__(kSvdThreads) k_svd_round(int n, int round, double2 *Ab, double2 *Wb,
+                                                           double tolj, int *rot) {
+  const int e = blockIdx.y;
+  const int64_t nn = (int64_t)n * n;
+  double2 *A = Ab + e * nn, *W = Wb + e * nn;
+  const int lane = threadIdx.x & 31;
+  const int pi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nn2 = (n + 1) & ~1;
+  if (pi >= nn2 / 2) return;
+  // circle method: player 0 fixed, the others rotate by `round`
+  const int a = pi, b = nn2 - 1 - pi;
+  const int p = (a == 0) ? 0 : ((a - 1 + round) % (nn2 - 1)) + 1;
+  const int q = (b == 0) ? 0 : ((b - 1 + round) % (nn2 - 1)) + 1;
+  if (p >= n || q >= n) return;
+  double2 *ap = A + (int64_t)p * n, *aq = A + (int64_t)q * n;
+  double al = 0, be = 0, gx = 0, gy = 0;
+  for (int i = lane; i < n; i += 32) {
+    const double2 u = ap[i], v = aq[i];
+    al += cabs2(u);
+    be += cabs2(v);
+    gx += u.x * v.x + u.y * v.y;   // conj(u) v
+    gy += u.x * v.y - u.y * v.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    gx += __shfl_xor_sync(0xffffffffu, gx, o);
+    gy += __shfl_xor_sync(0xffffffffu, gy, o);
+  }
+  const double g = hypot(gx, gy);
+  if (!(g > tolj * sqrt(al * be)) || al == 0.0 || be == 0.0) return;
+  // rotation that makes columns p and q orthogonal: with gamma = |g| e^{i phi},
+  // zeta = (be - al)/(2|g|), t the smaller root of t^2 + 2 zeta t - 1 = 0,
+  // a_p' = c a_p - s e^{-i phi} a_q,  a_q' = s e^{i phi} a_p + c a_q
+  const double zeta = (be - al) / (2.0 * g);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+  const double2 sp = make_double2(s * gx / g, s * gy / g);    // s e^{i phi}
+  const double2 spc = make_double2(sp.x, -sp.y);              // s e^{-i phi}
+  for (int i = lane; i < n; i += 32) {
+    const double2 u = ap[i], v = aq[i];
+    ap[i] = csub(cscale(u, c), cmul(spc, v));
+    aq[i] = cadd(cmul(sp, u), cscale(v, c));
+  }
+  double2 *wp = W + (int64_t)p * n, *wq = W + (int64_t)q * n;
+  for (int i = lane; i < n; i += 32) {
+    const double2 u = wp[i], v = wq[i];
+    wp[i] = csub(cscale(u, c), cmul(spc, v));
+    wq[i] = cadd(cmul(sp, u), cscale(v, c));
+  }
+  if (lane == 0) atomicAdd(&rot[e], 1);
+}
+
+// sigma_j = ||a_j||, sorted descending (ties by index); U = A/sigma, W permuted alike.
+__global__ void __launch_bounds__(1024) k_svd_finish(int n, double2 *Ab, const double2 *Wb, double2 *Ub,
+                                                     double2 *Wsb, double *sigb) {
   const int e = blockIdx.x;
   const int64_t nn = (int64_t)n * n;
-  double2 *A = Ab + e * nn, *W = Wb + e * nn, *U = Ub + e * nn, *Ws = Wsb + e * nn;
+  double2 *A = Ab + e * nn, *U = Ub + e * nn, *Ws = Wsb + e * nn;
+  const double2 *W = Wb + e * nn;
   double *sig = sigb + (int64_t)e * n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  for (int64_t idx = tid; idx < nn; idx += blockDim.x)
-    W[idx] = make_double2((idx % n) == (idx / n) ? 1.0 : 0.0, 0.0);
-  __shared__ int rot;
-  const int nn2 = (n + 1) & ~1;   // even number of players (one dummy if n is odd)
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) rot = 0;
-    __syncthreads();
-    for (int round = 0; round < nn2 - 1; ++round) {
-      for (int pi = warp; pi < nn2 / 2; pi += nwarp) {
-        // circle method: player 0 fixed, the others rotate by `round`
-        int a = pi, b = nn2 - 1 - pi;
-        int p = (a == 0) ? 0 : ((a - 1 + round) % (nn2 - 1)) + 1;
-        int q = (b == 0) ? 0 : ((b - 1 + round) % (nn2 - 1)) + 1;
-        if (p >= n || q >= n) continue;
-        double2 *ap = A + (int64_t)p * n, *aq = A + (int64_t)q * n;
-        double al = 0, be = 0, gx = 0, gy = 0;
-        for (int i = lane; i < n; i += 32) {
-          double2 u = ap[i], v = aq[i];
-          al += cabs2(u);
-          be += cabs2(v);
-          gx += u.x * v.x + u.y * v.y;   // conj(u) v
-          gy += u.x * v.y - u.y * v.x;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          gx += __shfl_xor_sync(0xffffffffu, gx, o);
-          gy += __shfl_xor_sync(0xffffffffu, gy, o);
-        }
-        const double g = hypot(gx, gy);
-        if (!(g > tolj * sqrt(al * be)) || al == 0.0 || be == 0.0) continue;
-        const double zeta = (be - al) / (2.0 * g);
-        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        const double2 ph = make_double2(gx / g, gy / g);      // e^{i phi}
-        const double2 sp = make_double2(s * ph.x, s * ph.y);  // s e^{i phi}
-        const double2 spc = make_double2(s * ph.x, -s * ph.y);// s e^{-i phi}
-        // a_p' = c a_p - s e^{-i phi} a_q ;  a_q' = s e^{i phi} a_p + c a_q
-        for (int i = lane; i < n; i += 32) {
-          double2 u = ap[i], v = aq[i];
-          ap[i] = csub(cscale(u, c), cmul(spc, v));
-          aq[i] = cadd(cmul(sp, u), cscale(v, c));
-        }
-        double2 *wp = W + (int64_t)p * n, *wq = W + (int64_t)q * n;
-        for (int i = lane; i < n; i += 32) {
-          double2 u = wp[i], v = wq[i];
-          wp[i] = csub(cscale(u, c), cmul(spc, v));
-          wq[i] = cadd(cmul(sp, u), cscale(v, c));
-        }
-        if (lane == 0) atomicAdd(&rot, 1);
-      }
-      __syncthreads();
-    }
-    if (rot == 0) break;
-    __syncthreads();
-  }
-  if (tid == 0) info[e] = (sweep >= max_sweeps) ? 1 : 0;
-  // column norms
+  __shared__ double s_sig[512];
+  __shared__ int rank_of[512];
   for (int j = warp; j < n; j += nwarp) {
     double s2 = 0;
     for (int i = lane; i < n; i += 32) s2 += cabs2(A[(int64_t)j * n + i]);
     for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    if (lane == 0) sig[j] = sqrt(s2);
+    if (lane == 0) s_sig[j] = sqrt(s2);
   }
   __syncthreads();
-  // rank of each sigma (descending, ties by index), then scatter sorted columns
-  __shared__ int rank_of[512];
   for (int j = tid; j < n; j += blockDim.x) {
-    double sj = sig[j];
+    const double sj = s_sig[j];
     int r = 0;
     for (int k = 0; k < n; ++k) {
-      double sk = sig[k];
+      const double sk = s_sig[k];
       r += (sk > sj) || (sk == sj && k < j);
     }
     rank_of[j] = r;
@@ -152,19 +163,14 @@ __global__ void __launch_bounds__(kSvdThreads) k_svd(int n, double2 *Ab, double2
   __syncthreads();
   for (int j = warp; j < n; j += nwarp) {
     const int r = rank_of[j];
-    const double sj = sig[j];
+    const double sj = s_sig[j];
     const double inv = sj > 0 ? 1.0 / sj : 0.0;
     for (int i = lane; i < n; i += 32) {
       U[(int64_t)r * n + i] = cscale(A[(int64_t)j * n + i], inv);
       Ws[(int64_t)r * n + i] = W[(int64_t)j * n + i];
     }
   }
-  __syncthreads();
-  // sorted singular values: write into A's first column as scratch first, then back
-  double *tmp = reinterpret_cast<double *>(A);
-  for (int j = tid; j < n; j += blockDim.x) tmp[rank_of[j]] = sig[j];
-  __syncthreads();
-  for (int j = tid; j < n; j += blockDim.x) sig[j] = tmp[j];
+  for (int j = tid; j < n; j += blockDim.x) sig[rank_of[j]] = s_sig[j];
 }
 
 __global__ void k_rank(int n_e, int n, const double *sig, double delta, int *mhat) {
@@ -594,8 +600,57 @@ cbs_status launch_hankel(int n_e, int L, int M, const double2 *mu, double2 *T, d
 cbs_status launch_svd(int n_e, int n, double2 *A, double2 *W, double2 *U, double2 *Ws,
                       double *sig, int *info, cudaStream_t st) {
   if (n > 512) { set_error("L*M must be <= 512"); return CBS_EINVAL; }
-  k_svd<<<n_e, kSvdThreads, 0, st>>>(n, A, W, U, Ws, sig, info, 1e-14, 60); cbs::count_launches(1);
+  const double tolj = 1e-14;
+  const int max_sweeps = 60;
+  const int nn2 = (n + 1) & ~1;
+  const int warps = kSvdThreads / 32;
+  dim3 grd_round((unsigned)ceil_div(nn2 / 2, warps), (unsigned)n_e, 1);
+  k_svd_init<<<dim3(64, (unsigned)n_e, 1), 256, 0, st>>>(n, W);
+  cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
+  int *rot = info;   // [n_e] rotation counters of the last sweep, then the info words
+  // capture one sweep
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const uint64_t c0 = launches_so_far();
+  CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = cudaMemsetAsync(rot, 0, (size_t)n_e * sizeof(int), st);
+  for (int r = 0; r < nn2 - 1 && ce == cudaSuccess; ++r) {
+    k_svd_round<<<grd_round, kSvdThreads, 0, st>>>(n, r, A, W, tolj, rot);
+    cbs::count_launches(1);
+    ce = cudaGetLastError();
+  }
+  cudaError_t ce2 = cudaStreamEndCapture(st, &graph);
+  const uint64_t per_sweep = launches_so_far() - c0;
+  uncount_launches(per_sweep);
+  if (ce != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(ce, "SVD round capture"); }
+  if (ce2 != cudaSuccess) return cuda_fail(ce2, "SVD sweep capture");
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return cuda_fail(ce, "SVD sweep instantiate");
+  std::vector<int> hrot(n_e);
+  int sweep = 0;
+  cbs_status status = CBS_OK;
+  for (; sweep < max_sweeps; ++sweep) {
+    ce = cudaGraphLaunch(exec, st);
+    count_launches(per_sweep);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hrot.data(), rot, (size_t)n_e * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) { status = cuda_fail(ce, "SVD sweep"); break; }
+    int any = 0;
+    for (int v : hrot) any |= (v != 0);
+    if (!any) break;
+  }
+  cudaGraphExecDestroy(exec);
+  if (status != CBS_OK) return status;
+  k_svd_finish<<<n_e, 1024, 0, st>>>(n, A, W, U, Ws, sig);
+  cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  // info: 1 if the sweep limit was reached (per energy: its last sweep still rotated)
+  std::vector<int> hinfo(n_e);
+  for (int e = 0; e < n_e; ++e) hinfo[e] = (sweep >= max_sweeps && hrot[e] != 0) ? 1 : 0;
+  CBS_CUDA(cudaMemcpyAsync(info, hinfo.data(), (size_t)n_e * sizeof(int), cudaMemcpyHostToDevice, st));
+  CBS_CUDA(cudaStreamSynchronize(st));
   return CBS_OK;
 }
 

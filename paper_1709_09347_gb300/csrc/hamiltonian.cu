@@ -222,7 +222,11 @@ static cbs_status create_impl(const cbs_grid *g, const double *v_loc, const cbs_
     v.wx[k] = -0.5 * c / (g->hx * g->hx);
     v.wy[k] = -0.5 * c / (g->hy * g->hy);
     v.wz[k] = -0.5 * c / (g->hz * g->hz);
+    v.w32[0][k] = (float)v.wx[k];
+    v.w32[1][k] = (float)v.wy[k];
+    v.w32[2][k] = (float)v.wz[k];
   }
+  v.diag_kin32 = (float)v.diag_kin;
   const size_t N = (size_t)v.n;
   for (size_t i = 0; i < N; ++i)
     if (!isfinite(v_loc[i])) { set_error("v_loc contains a non-finite value"); return CBS_EINVAL; }
@@ -233,7 +237,7 @@ static cbs_status create_impl(const cbs_grid *g, const double *v_loc, const cbs_
   if (s != CBS_OK) return s;
 
   // projectors
-  v.n_atoms = 0; v.n_proj = 0; h->nnz = 0;
+  v.n_atoms = 0; v.n_proj = 0; h->nnz = 0; v.np4 = 4;
   std::vector<int64_t> pt_ptr(N + 1, 0);
   if (P && P->n_atoms > 0) {
     if (P->n_proj < 1 || P->n_proj > kMaxProj) { set_error("n_proj must be 1..8"); return CBS_EINVAL; }
@@ -297,6 +301,21 @@ static cbs_status create_impl(const cbs_grid *g, const double *v_loc, const cbs_
     if ((s = upload(h, pt_ptr.data(), N + 1, &v.pt_ptr)) != CBS_OK) return s;
     if ((s = upload(h, pt_ent.data(), (size_t)nnz, &v.pt_ent)) != CBS_OK) return s;
     if ((s = upload(h, pt_atom.data(), (size_t)nnz, &v.pt_atom)) != CBS_OK) return s;
+    // packed per-entry records for the complex64 scatter (point order)
+    v.np4 = np <= 4 ? 4 : 8;
+    std::vector<int2> aw(nnz);
+    std::vector<float4> p4(np <= 4 ? nnz : 0);
+    for (int64_t q = 0; q < nnz; ++q) {
+      const int t = pt_ent[q];
+      aw[q] = make_int2(pt_atom[q], (int)P->sup_wrap[t]);
+      if (np <= 4) {
+        float pv[4] = {0, 0, 0, 0};
+        for (int mu = 0; mu < np; ++mu) pv[mu] = (float)P->sup_val[(int64_t)t * np + mu];
+        p4[q] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+      }
+    }
+    if ((s = upload(h, aw.data(), (size_t)nnz, &v.pt_aw)) != CBS_OK) return s;
+    if (np <= 4 && (s = upload(h, p4.data(), (size_t)nnz, &v.pt_p32)) != CBS_OK) return s;
   } else {
     if ((s = upload(h, pt_ptr.data(), N + 1, &v.pt_ptr)) != CBS_OK) return s;
   }

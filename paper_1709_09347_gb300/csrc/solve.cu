@@ -116,7 +116,7 @@ struct ResidualCheck {
   cbs_status alloc(const HamView &H, int n_, int L_) {
     n = n_; L = L_; N = H.n;
     const size_t vec = (size_t)2 * n * N * L * sizeof(double2);
-    const size_t dsz = (size_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * sizeof(double2);
+    const size_t dsz = (size_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * sizeof(double2);
     const size_t small = (size_t)2 * n * 64 * L * sizeof(double) + 3 * (size_t)2 * n * L * sizeof(double) +
                          (size_t)n * L * sizeof(int) + 4096;
     CBS_TRY(buf.alloc(vec + dsz + small + 1024));
@@ -413,7 +413,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
   size_t free_b = 0, total_b = 0;
   CBS_CUDA(cudaMemGetInfo(&free_b, &total_b));
   const size_t per_sys = ShiftedSolver::bytes_per_system(H, L, o.precision) +
-                         (size_t)2 * (H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * L * 16 * 2;
+                         (size_t)2 * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * 16 * 2;
   const size_t per_e = per_sys * n_int + (size_t)N * nLM * 16 + (size_t)4 * nLM * nLM * 16 * 6;
   int nb = o.energies_per_batch > 0 ? o.energies_per_batch : (int)std::max<size_t>(1, (free_b * 6 / 10) / per_e);
   nb = std::min(nb, n_e);
@@ -523,7 +523,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
       // vectors: P1 = Z Yc (m x cnt), rows / sigma, C2 = W_1 P1 (n x cnt), Psi^T = C2^T S^T
       DevBuf vb;
       const size_t psi_bytes = (size_t)N * cnt * sizeof(double2);
-      const size_t dsz = (size_t)(H.n_atoms ? H.n_atoms : 1) * (H.n_proj ? H.n_proj : 1) * cnt * sizeof(double2);
+      const size_t dsz = (size_t)(H.n_atoms ? H.n_atoms : 1) * H.np4 * cnt * sizeof(double2);
       CBS_TRY(vb.alloc(2 * psi_bytes + dsz + (size_t)n * cnt * 2 * sizeof(double2) + (size_t)cnt * 256 + 8192));
       char *p = vb.as<char>();
       auto take = [&](size_t sz) { char *r = p; p += (sz + 255) & ~(size_t)255; return (void *)r; };
