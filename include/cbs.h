@@ -148,6 +148,23 @@ cbs_status cbs_apply_ws(const cbs_hamiltonian *h, int n_sys, const double *z, co
                         int L, const void *X, void *Y, int dtype, void *workspace,
                         size_t workspace_bytes, void *stream);
 
+/* As cbs_apply, for callers that must not allocate device memory: code running under an
+ * allocator that owns all of the GPU's memory (a framework's memory pool, where a
+ * cudaMalloc behind its back can fail or fragment the pool), and latency-bound services
+ * that cannot afford cudaMalloc/cudaFree, which synchronise the device and stall other
+ * streams.  This call allocates nothing: its scratch (twists, energies and the projector
+ * coefficients) is a fixed 32 MiB array compiled into the library, present on every GPU
+ * that loads it until the process exits.  The paper has no counterpart to this entry point.
+ * z, E: HOST arrays [n_sys]; X, Y: DEVICE [n_sys][N][L] of type dtype; runs on `stream`
+ * and does not synchronise.  Sizes whose scratch (about n_sys*L*n_atoms*4*16 bytes in
+ * complex128, half that in complex64) exceed the 32 MiB return CBS_EINVAL.  The first call
+ * on a device looks up the array's device address (with that device current); make that
+ * first call before any stream capture.  All calls share the one array: calls whose GPU
+ * work overlaps (on different streams or threads) race and must be serialised by the
+ * caller. */
+cbs_status cbs_apply_noalloc(const cbs_hamiltonian *h, int n_sys, const double *z, const double *E,
+                             int L, const void *X, void *Y, int dtype, void *stream);
+
 /* Shifted solves of §3.2 for a batch of n_sys points: BiCG on P(z_s) Y[s] = B and, as
  * its dual, P(z_s)^dagger Yd[s] = B (= P(1/conj z_s) Yd[s] = B).
  * z, E: host arrays [n_sys]; B: DEVICE [N][L] complex128 (shared by all systems);

@@ -27,7 +27,7 @@ EXPORTS = (
     "cbs_hamiltonian_norms", "cbs_apply", "cbs_solve_shifted", "cbs_solve", "cbs_result_count",
     "cbs_result_get", "cbs_result_stats", "cbs_result_all", "cbs_result_moments", "cbs_result_iters",
     "cbs_result_timing", "cbs_result_profile", "cbs_result_free", "cbs_last_error",
-    "cbs_kernel_launches", "cbs_apply_workspace_size", "cbs_apply_ws",
+    "cbs_kernel_launches", "cbs_apply_workspace_size", "cbs_apply_ws", "cbs_apply_noalloc",
 )
 
 
@@ -105,6 +105,7 @@ def load():
     lib.cbs_apply_workspace_size.argtypes = [V, I, I, I]
     lib.cbs_apply_workspace_size.restype = ct.c_size_t
     lib.cbs_apply_ws.argtypes = [V, I, V, V, I, V, V, I, V, ct.c_size_t, V]
+    lib.cbs_apply_noalloc.argtypes = [V, I, P(D), P(D), I, V, V, I, V]
     lib.cbs_kernel_launches.argtypes = []
     lib.cbs_kernel_launches.restype = ct.c_uint64
     _lib = lib
