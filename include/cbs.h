@@ -102,7 +102,7 @@ typedef struct {
   int max_sweeps;       /* FP64 residual updates (residual replacements) (200)           */
   int inner_max_iter;   /* iteration cap of one complex64 phase (1000)                   */
   int stall_sweeps;     /* updates without halving the FP64 residual before the columns
-                           left are finished by FP64 BiCG (4)                              */
+                           left are finished by FP64 BiCG (12)                             */
   int energies_per_batch; /* energies solved together; 0 = as many as fit (0)            */
   int profile;          /* 1: time every operator-apply launch with CUDA events (0)      */
   void *stream;         /* cudaStream_t to run on; NULL = the library's own stream       */
@@ -184,6 +184,21 @@ cbs_status cbs_solve_shifted(const cbs_hamiltonian *h, int n_sys, const double *
 cbs_status cbs_solve(const cbs_hamiltonian *h, const double *energies, int n_e,
                      const cbs_contour *contour, int L, int M, const void *V,
                      const cbs_options *opt, cbs_result **out);
+
+/* Objective of the ring solves and its gradient (reverse mode, adjoint solves).
+ * J = sum_{c=1,2} sum_j c_j^(c) ||Y_j^(c)||_F^2, with Y_j^(c) = P(z_j^(c))^{-1} V the solutions
+ * of the shifted systems of §3.2 (Eq. (9)-(11)) at energy E, and real weights
+ * c_j^(c) = Re(s_c w_j^(c) sum_{k<M} (z_j^(c))^k), s_1 = +1, s_2 = -1 (the |Y|^2-weighted trace
+ * of the moment sum).  If grad_vloc or grad_E is non-NULL, one adjoint BiCG batch gives
+ * G = P^{-dagger} Y and
+ *   grad_vloc[i] = dJ/dV_loc[i] = sum 2 c Re sum_col conj(G[i,col]) Y[i,col]   (host or device, [N]),
+ *   *grad_E      = dJ/dE        = -sum 2 c Re tr(G^dagger Y).
+ * The forward solutions are recomputed by every call (nothing is kept between a call that
+ * only evaluates J and one that asks for the gradient).  V: [N][L] complex128, host or
+ * device.  The adjoint solves run in FP64 to opt->tol. */
+cbs_status cbs_objective(const cbs_hamiltonian *h, double E, const cbs_contour *contour, int L,
+                         int M, const void *V, const cbs_options *opt, double *J,
+                         double *grad_vloc, double *grad_E);
 
 /* Per-energy results.  Eigenpairs are those with lambda_min < |lambda| < 1/lambda_min and
  * residual <= rho_max, sorted by |lambda| then arg(lambda); vectors have unit 2-norm and

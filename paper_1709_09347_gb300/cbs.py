@@ -28,6 +28,7 @@ EXPORTS = (
     "cbs_result_get", "cbs_result_stats", "cbs_result_all", "cbs_result_moments", "cbs_result_iters",
     "cbs_result_timing", "cbs_result_profile", "cbs_result_free", "cbs_last_error",
     "cbs_kernel_launches", "cbs_apply_workspace_size", "cbs_apply_ws", "cbs_apply_noalloc",
+    "cbs_objective",
 )
 
 
@@ -106,6 +107,7 @@ def load():
     lib.cbs_apply_workspace_size.restype = ct.c_size_t
     lib.cbs_apply_ws.argtypes = [V, I, V, V, I, V, V, I, V, ct.c_size_t, V]
     lib.cbs_apply_noalloc.argtypes = [V, I, P(D), P(D), I, V, V, I, V]
+    lib.cbs_objective.argtypes = [V, D, P(Contour), I, I, V, P(Options), P(D), P(D), P(D)]
     lib.cbs_kernel_launches.argtypes = []
     lib.cbs_kernel_launches.restype = ct.c_uint64
     _lib = lib
@@ -318,3 +320,45 @@ class ApplyPlan:
                                    ct.c_void_p(Y.data_ptr()), self.dt, ct.c_void_p(self.ws.data_ptr()),
                                    self.ws.numel(), _stream_ptr(torch)))
         return Y
+
+
+def objective(H: Hamiltonian, E, lambda_min, n_int, L, M, V, opts: Options | None = None,
+              grad: bool = False):
+    """J = sum_c sum_j c_j ||Y_j||_F^2 of the ring solves at energy E (cbs_objective); with
+    grad=True also (dJ/dV_loc as a numpy array [N], dJ/dE)."""
+    lib = load()
+    ctr = Contour(float(lambda_min), int(n_int))
+    Vh = np.ascontiguousarray(V, dtype=np.complex128)
+    o = opts or options()
+    J = ct.c_double()
+    gE = ct.c_double()
+    gV = np.zeros(H.n) if grad else None
+    _check(lib.cbs_objective(H.handle, float(E), ct.byref(ctr), int(L), int(M), ct.c_void_p(Vh.ctypes.data),
+                             ct.byref(o), ct.byref(J), _dptr(gV) if grad else None,
+                             ct.byref(gE) if grad else None))
+    return (J.value, gV, gE.value) if grad else J.value
+
+
+def ring_objective(vloc, E, grid, projectors, lambda_min, n_int, L, M, V, opts: Options | None = None):
+    """Differentiable J(V_loc, E): a torch.autograd.Function whose backward runs the adjoint
+    solves on the device (the forward solutions are recomputed, not stored)."""
+    import torch
+
+    class _RingObjective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v, e):
+            H = Hamiltonian(grid, v.detach().cpu().numpy(), projectors)
+            J = objective(H, float(e), lambda_min, n_int, L, M, V, opts)
+            ctx.save_for_backward(v, e)
+            return torch.tensor(J, dtype=torch.float64, device=v.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            v, e = ctx.saved_tensors
+            H = Hamiltonian(grid, v.detach().cpu().numpy(), projectors)
+            _, gV, gE = objective(H, float(e), lambda_min, n_int, L, M, V, opts, grad=True)
+            gv = torch.from_numpy(gV).to(v.device, v.dtype) * gJ
+            ge = torch.tensor(gE, dtype=e.dtype, device=e.device) * gJ
+            return gv, ge
+
+    return _RingObjective.apply(vloc, E)

@@ -44,7 +44,7 @@ extern "C" cbs_status cbs_options_default(cbs_options *o) {
   o->inner_tol = 0.1;
   o->max_sweeps = 200;
   o->inner_max_iter = 1000;
-  o->stall_sweeps = 4;
+  o->stall_sweeps = 12;
   o->energies_per_batch = 0;
   o->stream = nullptr;
   return CBS_OK;

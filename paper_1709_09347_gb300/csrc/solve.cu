@@ -682,3 +682,24 @@ extern "C" cbs_status cbs_result_profile(const cbs_result *r, int dtype, double 
 }
 
 extern "C" void cbs_result_free(cbs_result *r) { delete r; }
+
+// Ring solves for the objective/adjoint entry point: n systems at the outer-circle points
+// and their duals; *Y_out points to [2n][N][L] FP64 solutions owned by *owner (release with
+// cbs_internal_ring_release).
+cbs_status cbs_internal_ring_solve(const cbs_hamiltonian *h, int n, int L, const double2 *zs,
+                                   const double *Es, const double2 *dV, const cbs_options &o,
+                                   cudaStream_t st, double2 **Y_out, void **owner) {
+  ShiftedSolver *S = new (std::nothrow) ShiftedSolver();
+  if (!S) { set_error("host allocation failed"); return CBS_ENOMEM; }
+  *owner = S;
+  cbs_status s = S->run(h->v, n, L, zs, Es, dV, o, st);
+  if (s != CBS_OK) return s;
+  *Y_out = S->Y;
+  int fl = 0;
+  for (int f : S->flags) fl |= f;
+  if (fl & 2) { set_error("BiCG breakdown in some column"); return CBS_EBREAKDOWN; }
+  if (fl & 1) { set_error("BiCG did not converge in some column"); return CBS_ENOCONV; }
+  return CBS_OK;
+}
+
+void cbs_internal_ring_release(void *owner) { delete (ShiftedSolver *)owner; }

@@ -124,7 +124,7 @@ def test_solve_c2_vs_oracle_golden(precision, lam_tol):
     g = np.load(os.path.join(os.path.dirname(__file__), "golden", "c2_oracle.npz"))
     wl = synth.workload("c2")
     idx = [int(i) for i in g["energy_index"]]
-    res = _gpu_solve(wl, wl.energies[idx], precision, tol=1e-10)
+    res = _gpu_solve(wl, wl.energies[idx], precision, tol=float(g["tol"]))
     op = CellOperator(wl.grid, wl.vloc, wl.projectors)
     for e, i in enumerate(idx):
         r = res.energies[e]
