@@ -23,7 +23,8 @@ kept if lambda_min < |lambda| < 1/lambda_min (Eq. (5)) and rho <= rho_max, norma
 arg(lambda), and k = -i ln(lambda) / a = (arg(lambda) - i ln|lambda|) / a (§2, Eq. (3)).
 
 A Rayleigh-Ritz variant (not in the paper) projects the three blocks onto an
-orthonormal basis of span(S) and solves the small QEP by companion linearisation.
+orthonormal basis of span(S W_1) (the part of the moment space the Hankel rank cut
+keeps) and solves the small QEP by companion linearisation.
 
 Pins (tests/test_oracle_ss.py): moments of a diagonal QEP against the residue sum;
 the in-ring eigenvalues of tiny cells against the dense linearisation and against the
@@ -91,7 +92,8 @@ def moments(Y1, Y2, lambda_min, n_int, V, M):
 
 
 def hankel_extract(S, mu, M, delta):
-    """Algorithm 1, lines 2-4: returns (lam, psi, rank, sigma)."""
+    """Algorithm 1, Hankel extraction (SVD of T, rank cut, reduced eigenproblem, vectors):
+    returns (lam, psi, rank, sigma)."""
     L = mu.shape[1]
     T = np.zeros((L * M, L * M), complex)
     Tl = np.zeros((L * M, L * M), complex)
@@ -164,30 +166,48 @@ def ss_hankel(op, E, lambda_min, n_int, V, M, delta=1e-10, tol=1e-10, rho_max=1e
                     mu if keep_moments else None, S[:M] if keep_moments else None)
 
 
+def rr_basis(S, mu, M, delta, basis_cut=1e-7):
+    """Orthonormal basis of span(S W_1): W_1 are the right singular vectors of the block
+    Hankel matrix T kept by the delta cut of Algorithm 1; columns of S W_1 whose
+    singular values fall below basis_cut * the largest are dropped."""
+    L = mu.shape[1]
+    T = np.zeros((L * M, L * M), complex)
+    for i in range(M):
+        for j in range(M):
+            T[i * L:(i + 1) * L, j * L:(j + 1) * L] = mu[i + j]
+    _, sig, Wh = np.linalg.svd(T)
+    m_hat = int(np.sum(sig >= delta * sig[0])) if sig[0] > 0 else 0
+    Shat = np.concatenate([S[k] for k in range(M)], axis=1)
+    Z = Shat @ Wh[:m_hat].conj().T
+    Uz, sz, _ = np.linalg.svd(Z, full_matrices=False)
+    r = int(np.sum(sz >= basis_cut * sz[0])) if len(sz) and sz[0] > 0 else 0
+    return Uz[:, :r], m_hat, sig
+
+
 def ss_rayleigh_ritz(op, E, lambda_min, n_int, V, M, delta=1e-10, tol=1e-10, rho_max=1e-8,
-                     max_iter=20000, S=None):
-    """Rayleigh-Ritz variant: basis of span(S_0..S_{M-1}), small QEP by linearisation."""
+                     max_iter=20000, S=None, mu=None):
+    """Rayleigh-Ritz variant (not in the paper): the QEP's three blocks projected onto the
+    basis of rr_basis, the small QEP lambda^2 A2 + lambda A1 + A0 solved by companion
+    linearisation, Ritz vectors x = Q u filtered like the Hankel pairs."""
     iters = np.zeros((n_int, V.shape[1]), int)
     if S is None:
         Y1, Y2, iters = solve_ring(op, E, lambda_min, n_int, V, tol=tol, max_iter=max_iter)
-        S, _ = moments(Y1, Y2, lambda_min, n_int, V, M)
-    Shat = np.concatenate([S[k] for k in range(M)], axis=1)
-    U, sig, _ = np.linalg.svd(Shat, full_matrices=False)
-    m_hat = int(np.sum(sig >= delta * sig[0]))
-    Qb = U[:, :m_hat]
+        S, mu = moments(Y1, Y2, lambda_min, n_int, V, M)
+    Qb, m_hat, sig = rr_basis(S, mu, M, delta)
+    r = Qb.shape[1]
     H0Q, HpQ, HmQ = apply_blocks(op, Qb)
     A2 = Qb.conj().T @ HpQ
     A1 = Qb.conj().T @ (H0Q - E * Qb)
     A0 = Qb.conj().T @ HmQ
-    I = np.eye(m_hat)
-    Z = np.zeros((m_hat, m_hat))
+    I = np.eye(r)
+    Z = np.zeros((r, r))
     Amat = np.block([[Z, I], [-A0, -A1]])
     Bmat = np.block([[I, Z], [Z, A2]])
     w, v = sla.eig(Amat, Bmat)
     fin = np.isfinite(w) & (np.abs(w) > 0)
-    w, v = w[fin], v[:m_hat, fin]
+    w, v = w[fin], v[:r, fin]
     X = Qb @ v
     norms = op.frobenius(E)
     res_all = residuals(op, E, w, X, norms)
     lam, k, res, Xn = filter_sort(w, X, res_all, lambda_min, op.grid.a, rho_max)
-    return SSResult(lam, k, res, Xn, m_hat, sig, w, res_all, iters)
+    return SSResult(lam, k, res, Xn, r, sig, w, res_all, iters)

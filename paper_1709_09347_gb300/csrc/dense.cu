@@ -1,4 +1,4 @@
-// Small dense FP64 stage of Algorithm 1 (lines 2-4), on the device.
+// Small dense FP64 stage of Algorithm 1 (Hankel SVD, rank cut, reduced eigenproblem), on the device.
 //
 //   T = [mu_{i+j-2}], T^< = [mu_{i+j-1}]  (block Hankel, L*M square)
 //   T = U Sigma W^dagger (one-sided Jacobi SVD), rank m_hat: sigma_i >= delta sigma_1
@@ -281,9 +281,12 @@ __global__ void k_scale_cols(int n, int ldm, const int *mhat, const double *sig,
 // eigenvalues (those strictly inside the ring), compacted into Yc (m x n_ring) and
 // transformed by Z outside this kernel.
 constexpr int kEigThreads = 512;
+// shift: 0 selects eigenvalues tau inside the ring; otherwise the eigenvalues are mu of a
+// shifted-and-inverted problem, lambda = shift + 1/mu is tested and written back to tau.
 __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, double2 *Bb, double2 *Zb,
                                                      double2 *taub, double2 *Ycb, int *nring,
-                                                     int *ringidx, double lambda_min, int *info) {
+                                                     int *ringidx, double lambda_min, int *info,
+                                                     double2 shift, int shifted) {
   const int e = blockIdx.x;
   const int m = mhat[e];
   const int64_t nn = (int64_t)ld * ld;
@@ -448,7 +451,13 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
   if (tid == 0) {
     int cnt = 0;
     for (int k = 0; k < m; ++k) {
-      const double r = cabsd(tau[k]);
+      double2 lam = tau[k];
+      if (shifted) {
+        lam = (cabs2(lam) > 0) ? cadd(shift, cdiv(make_double2(1.0, 0.0), lam))
+                               : make_double2(INFINITY, INFINITY);
+        tau[k] = lam;   // the back substitution below reads the Schur form, not tau
+      }
+      const double r = cabsd(lam);
       if (!sh_fail && isfinite(r) && r > lambda_min && r < 1.0 / lambda_min) ridx[cnt++] = k;
     }
     nring[e] = cnt;
@@ -669,9 +678,11 @@ cbs_status launch_scale(int n_e, int rows, int ld, const int *mhat, const double
 
 cbs_status launch_eig(int n_e, int ld, const int *mhat, double2 *B, double2 *Z, double2 *tau,
                       double2 *Yc, int *nring, int *ringidx, double lambda_min, int *info,
-                      cudaStream_t st) {
-  if (ld > 512) { set_error("L*M must be <= 512"); return CBS_EINVAL; }
-  k_eig<<<n_e, kEigThreads, 0, st>>>(ld, mhat, B, Z, tau, Yc, nring, ringidx, lambda_min, info); cbs::count_launches(1);
+                      cudaStream_t st, double2 shift, int shifted) {
+  if (ld > 512) { set_error("eigenproblem larger than 512"); return CBS_EINVAL; }
+  k_eig<<<n_e, kEigThreads, 0, st>>>(ld, mhat, B, Z, tau, Yc, nring, ringidx, lambda_min, info, shift,
+                                     shifted);
+  cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }

@@ -28,7 +28,7 @@ cbs_status launch_scale(int n_e, int rows, int ld, const int *mhat, const double
                         int rows_scale, cudaStream_t st);
 cbs_status launch_eig(int n_e, int ld, const int *mhat, double2 *B, double2 *Z, double2 *tau,
                       double2 *Yc, int *nring, int *ringidx, double lambda_min, int *info,
-                      cudaStream_t st);
+                      cudaStream_t st, double2 shift = make_double2(0, 0), int shifted = 0);
 cbs_status launch_filter(int64_t N, int cnt, const double2 *tau_ring, const double2 *Psi,
                          const double2 *Res, double *stats, double nHp, double nA, double nHm,
                          double rho_max, double a_cell, double *rho_all, int *n_keep, int *perm,

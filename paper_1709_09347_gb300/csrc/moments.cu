@@ -1,4 +1,4 @@
-// Contour quadrature and moment accumulation (Algorithm 1, line 1, on the ring of §3.2).
+// Contour quadrature and moment accumulation (Algorithm 1, first step, on the ring of §3.2).
 //
 //   S_k  = sum_j w_j^(1) (z_j^(1))^k Y_j^(1) - sum_j w_j^(2) (z_j^(2))^k Y_j^(2),  k < M
 //   mu_k = V^dagger S_k = sum_j w_j^(1) (z_j^(1))^k G_j - w_j^(2) (z_j^(2))^k G~_j, k < 2M

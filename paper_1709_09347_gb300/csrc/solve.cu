@@ -12,6 +12,11 @@
 
 using namespace cbs;
 
+cbs_status cbs_internal_rr(const cbs_hamiltonian *h, double E, const double2 *S, const double2 *Ws,
+                           int n, int m, double lambda_min, cudaStream_t st, void **ws_out,
+                           int *cnt_out, double2 **lam_out, double2 **Psi_out,
+                           std::vector<double2> *lam_all, int *rank_out);
+
 struct cbs_energy_result {
   std::vector<double2> lam, k, vec, lam_all, mu;
   std::vector<double> rho, res_all;
@@ -475,10 +480,14 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
     CBS_TRY(launch_rank(ne, n, sig, o.delta, mhat, st));
     const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
     // C1 = T^< W (all n columns), Bm = U^dagger C1, then columns j < m_hat scaled by 1/sigma_j
-    CBS_TRY(zgemm(0, 0, n, n, n, one, Tl, n, nn, Ws, n, nn, zero, C1, n, nn, ne, st));
-    CBS_TRY(zgemm(2, 0, n, n, n, one, U, n, nn, C1, n, nn, zero, Bm, n, nn, ne, st));
-    CBS_TRY(launch_scale(ne, n, n, mhat, sig, Bm, 0, st));
-    CBS_TRY(launch_eig(ne, n, mhat, Bm, Z, tau, Yc, nring, ridx, ct->lambda_min, ieig, st));
+    if (o.extraction == CBS_HANKEL) {
+      CBS_TRY(zgemm(0, 0, n, n, n, one, Tl, n, nn, Ws, n, nn, zero, C1, n, nn, ne, st));
+      CBS_TRY(zgemm(2, 0, n, n, n, one, U, n, nn, C1, n, nn, zero, Bm, n, nn, ne, st));
+      CBS_TRY(launch_scale(ne, n, n, mhat, sig, Bm, 0, st));
+      CBS_TRY(launch_eig(ne, n, mhat, Bm, Z, tau, Yc, nring, ridx, ct->lambda_min, ieig, st));
+    } else {
+      CBS_CUDA(cudaMemsetAsync(small + ne, 0, (size_t)3 * ne * sizeof(int), st));
+    }
     std::vector<int> hsmall(4 * ne);
     std::vector<double> hsig((size_t)ne * n);
     std::vector<double2> htau((size_t)ne * n);
@@ -519,64 +528,101 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
       if (fl & 2) ret = (ret == CBS_OK ? CBS_EBREAKDOWN : ret);
       else if (fl & 1) ret = (ret == CBS_OK ? CBS_ENOCONV : ret);
       else if (m == n && ret == CBS_OK) ret = CBS_WRANK;
-      if (cnt == 0) continue;
-      // vectors: P1 = Z Yc (m x cnt), rows / sigma, C2 = W_1 P1 (n x cnt), Psi^T = C2^T S^T
-      DevBuf vb;
-      const size_t psi_bytes = (size_t)N * cnt * sizeof(double2);
-      const size_t dsz = (size_t)(H.n_atoms ? H.n_atoms : 1) * H.np4 * cnt * sizeof(double2);
-      CBS_TRY(vb.alloc(2 * psi_bytes + dsz + (size_t)n * cnt * 2 * sizeof(double2) + (size_t)cnt * 256 + 8192));
-      char *p = vb.as<char>();
-      auto take = [&](size_t sz) { char *r = p; p += (sz + 255) & ~(size_t)255; return (void *)r; };
-      double2 *Psi = (double2 *)take(psi_bytes);
-      double2 *Res = (double2 *)take(psi_bytes);
-      double2 *Dd = (double2 *)take(dsz);
-      double2 *P1 = (double2 *)take((size_t)n * cnt * sizeof(double2));
-      double2 *C2 = (double2 *)take((size_t)n * cnt * sizeof(double2));
-      double2 *twr = (double2 *)take((size_t)cnt * sizeof(double2));
-      double *stats = (double *)take((size_t)cnt * 4 * sizeof(double));
-      double *rho_all = (double *)take((size_t)cnt * sizeof(double));
-      int *perm = (int *)take((size_t)cnt * sizeof(int));
-      double2 *lam_o = (double2 *)take((size_t)cnt * sizeof(double2));
-      double2 *k_o = (double2 *)take((size_t)cnt * sizeof(double2));
-      double *rho_o = (double *)take((size_t)cnt * sizeof(double));
-      double2 *scale = (double2 *)take((size_t)cnt * sizeof(double2));
-      int *nkeep = (int *)take(256);
-      double *Ed = (double *)take(256);
-      CBS_CUDA(cudaMemcpyAsync(Ed, &Ee, sizeof(double), cudaMemcpyHostToDevice, st));
-      CBS_TRY(zgemm(0, 0, m, cnt, m, one, Z + nn * e, n, 0, Yc + nn * e, n, 0, zero, P1, n, 0, 1, st));
-      k_scale_rows<<<64, 256, 0, st>>>(m, cnt, n, sig + (size_t)e * n, P1); cbs::count_launches(1);
-      CBS_CUDA(cudaGetLastError());
-      CBS_TRY(zgemm(0, 0, n, cnt, m, one, Ws + nn * e, n, 0, P1, n, 0, zero, C2, n, 0, 1, st));
-      // Psi (row-major N x cnt) = S (row-major N x n) C2  <=>  Psi^T = C2^T S^T (column-major)
-      CBS_TRY(zgemm(1, 0, cnt, (int)N, n, one, C2, n, 0, Sm + (size_t)e * N * n, n, 0, zero, Psi, cnt, 0, 1, st));
-      k_gather_tau<<<ceil_div(cnt, 128), 128, 0, st>>>(cnt, tau + (size_t)e * n, ridx + (size_t)e * n, twr); cbs::count_launches(1);
-      CBS_CUDA(cudaGetLastError());
-      CBS_TRY(apply_P<double>(H, 1, cnt, Psi, Res, twr, true, Ed, Dd, nullptr, st));
-      double nHp, nA, nHm;
-      cbs_hamiltonian_norms(h, Ee, &nHp, &nA, &nHm);
-      const double a_cell = h->hz * H.nz;
-      CBS_TRY(launch_filter(N, cnt, twr, Psi, Res, stats, nHp, nA, nHm, o.rho_max, a_cell, rho_all,
-                            nkeep, perm, lam_o, k_o, rho_o, scale, st));
-      int hk = 0;
-      std::vector<double> hrho(cnt);
-      std::vector<int> hridx(cnt);
-      CBS_CUDA(cudaMemcpyAsync(&hk, nkeep, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaMemcpyAsync(hrho.data(), rho_all, cnt * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaMemcpyAsync(hridx.data(), ridx + (size_t)e * n, cnt * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaStreamSynchronize(st));
-      for (int r = 0; r < cnt; ++r) R.res_all[hridx[r]] = hrho[r];
-      R.st.n_kept = hk;
-      R.lam.resize(hk);
-      R.k.resize(hk);
-      R.rho.resize(hk);
-      R.vec.resize((size_t)N * hk);
-      if (hk > 0) {
-        CBS_TRY(launch_gather_vectors(N, cnt, hk, Psi, perm, scale, Res, st));
-        CBS_CUDA(cudaMemcpyAsync(R.lam.data(), lam_o, hk * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        CBS_CUDA(cudaMemcpyAsync(R.k.data(), k_o, hk * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        CBS_CUDA(cudaMemcpyAsync(R.rho.data(), rho_o, hk * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CBS_CUDA(cudaMemcpyAsync(R.vec.data(), Res, (size_t)N * hk * sizeof(double2), cudaMemcpyDeviceToHost, st));
+      // residual of every candidate (lambda in the ring), filter, sort, normalise, copy out
+      auto finish = [&](int cnt, double2 *Psi, const double2 *twr_src, const int *ring_host) -> cbs_status {
+        DevBuf vb;
+        const size_t psi_bytes = (size_t)N * cnt * sizeof(double2);
+        const size_t dsz = (size_t)(H.n_atoms ? H.n_atoms : 1) * H.np4 * cnt * sizeof(double2);
+        CBS_TRY(vb.alloc(psi_bytes + dsz + (size_t)cnt * 256 + 8192));
+        char *p = vb.as<char>();
+        auto take = [&](size_t sz) { char *r = p; p += (sz + 255) & ~(size_t)255; return (void *)r; };
+        double2 *Res = (double2 *)take(psi_bytes);
+        double2 *Dd = (double2 *)take(dsz);
+        double2 *twr = (double2 *)take((size_t)cnt * sizeof(double2));
+        double *stats = (double *)take((size_t)cnt * 4 * sizeof(double));
+        double *rho_all = (double *)take((size_t)cnt * sizeof(double));
+        int *perm = (int *)take((size_t)cnt * sizeof(int));
+        double2 *lam_o = (double2 *)take((size_t)cnt * sizeof(double2));
+        double2 *k_o = (double2 *)take((size_t)cnt * sizeof(double2));
+        double *rho_o = (double *)take((size_t)cnt * sizeof(double));
+        double2 *scale = (double2 *)take((size_t)cnt * sizeof(double2));
+        int *nkeep = (int *)take(256);
+        double *Ed = (double *)take(256);
+        CBS_CUDA(cudaMemcpyAsync(Ed, &Ee, sizeof(double), cudaMemcpyHostToDevice, st));
+        CBS_CUDA(cudaMemcpyAsync(twr, twr_src, (size_t)cnt * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        CBS_TRY(apply_P<double>(H, 1, cnt, Psi, Res, twr, true, Ed, Dd, nullptr, st));
+        double nHp, nA, nHm;
+        cbs_hamiltonian_norms(h, Ee, &nHp, &nA, &nHm);
+        const double a_cell = h->hz * H.nz;
+        CBS_TRY(launch_filter(N, cnt, twr, Psi, Res, stats, nHp, nA, nHm, o.rho_max, a_cell, rho_all,
+                              nkeep, perm, lam_o, k_o, rho_o, scale, st));
+        int hk = 0;
+        std::vector<double> hrho(cnt);
+        CBS_CUDA(cudaMemcpyAsync(&hk, nkeep, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaMemcpyAsync(hrho.data(), rho_all, cnt * sizeof(double), cudaMemcpyDeviceToHost, st));
         CBS_CUDA(cudaStreamSynchronize(st));
+        if (ring_host)
+          for (int r = 0; r < cnt; ++r) R.res_all[ring_host[r]] = hrho[r];
+        R.st.n_kept = hk;
+        R.lam.resize(hk);
+        R.k.resize(hk);
+        R.rho.resize(hk);
+        R.vec.resize((size_t)N * hk);
+        if (hk > 0) {
+          CBS_TRY(launch_gather_vectors(N, cnt, hk, Psi, perm, scale, Res, st));
+          CBS_CUDA(cudaMemcpyAsync(R.lam.data(), lam_o, hk * sizeof(double2), cudaMemcpyDeviceToHost, st));
+          CBS_CUDA(cudaMemcpyAsync(R.k.data(), k_o, hk * sizeof(double2), cudaMemcpyDeviceToHost, st));
+          CBS_CUDA(cudaMemcpyAsync(R.rho.data(), rho_o, hk * sizeof(double), cudaMemcpyDeviceToHost, st));
+          CBS_CUDA(cudaMemcpyAsync(R.vec.data(), Res, (size_t)N * hk * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        }
+        CBS_CUDA(cudaStreamSynchronize(st));
+        return CBS_OK;
+      };
+      if (o.extraction == CBS_RR) {
+        void *rws = nullptr;
+        int rcnt = 0, rrank = 0;
+        double2 *rlam = nullptr, *rPsi = nullptr;
+        std::vector<double2> rall;
+        cbs_status rs = m > 0 ? cbs_internal_rr(h, Ee, Sm + (size_t)e * N * n, Ws + nn * e, n, m,
+                                                ct->lambda_min, st, &rws, &rcnt, &rlam, &rPsi, &rall,
+                                                &rrank)
+                              : CBS_OK;
+        if (rs == CBS_OK) {
+          R.st.rank = rrank;
+          R.st.n_extracted = (int)rall.size();
+          R.lam_all = rall;
+          R.res_all.assign(rall.size(), NAN);
+          if (rcnt > 0) rs = finish(rcnt, rPsi, rlam, nullptr);
+        }
+        cudaStreamSynchronize(st);
+        if (rws) cudaFree(rws);
+        if (rs != CBS_OK) return rs;
+        continue;
+      }
+      if (cnt == 0) continue;
+      {
+        // vectors: P1 = Z Yc (m x cnt), rows / sigma, C2 = W_1 P1 (n x cnt), Psi^T = C2^T S^T
+        DevBuf vb;
+        const size_t psi_bytes = (size_t)N * cnt * sizeof(double2);
+        CBS_TRY(vb.alloc(psi_bytes + (size_t)n * cnt * 2 * sizeof(double2) + (size_t)cnt * 64 + 4096));
+        char *p = vb.as<char>();
+        auto take = [&](size_t sz) { char *r = p; p += (sz + 255) & ~(size_t)255; return (void *)r; };
+        double2 *Psi = (double2 *)take(psi_bytes);
+        double2 *P1 = (double2 *)take((size_t)n * cnt * sizeof(double2));
+        double2 *C2 = (double2 *)take((size_t)n * cnt * sizeof(double2));
+        double2 *twr = (double2 *)take((size_t)cnt * sizeof(double2));
+        CBS_TRY(zgemm(0, 0, m, cnt, m, one, Z + nn * e, n, 0, Yc + nn * e, n, 0, zero, P1, n, 0, 1, st));
+        k_scale_rows<<<64, 256, 0, st>>>(m, cnt, n, sig + (size_t)e * n, P1); cbs::count_launches(1);
+        CBS_CUDA(cudaGetLastError());
+        CBS_TRY(zgemm(0, 0, n, cnt, m, one, Ws + nn * e, n, 0, P1, n, 0, zero, C2, n, 0, 1, st));
+        // Psi (row-major N x cnt) = S (row-major N x n) C2  <=>  Psi^T = C2^T S^T (column-major)
+        CBS_TRY(zgemm(1, 0, cnt, (int)N, n, one, C2, n, 0, Sm + (size_t)e * N * n, n, 0, zero, Psi, cnt, 0, 1, st));
+        k_gather_tau<<<ceil_div(cnt, 128), 128, 0, st>>>(cnt, tau + (size_t)e * n, ridx + (size_t)e * n, twr); cbs::count_launches(1);
+        CBS_CUDA(cudaGetLastError());
+        std::vector<int> hridx(cnt);
+        CBS_CUDA(cudaMemcpyAsync(hridx.data(), ridx + (size_t)e * n, cnt * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaStreamSynchronize(st));
+        CBS_TRY(finish(cnt, Psi, twr, hridx.data()));
       }
     }
     CBS_TRY(lap(&res->ms_extract));
@@ -603,10 +649,6 @@ extern "C" cbs_status cbs_solve(const cbs_hamiltonian *h, const double *energies
   }
   cbs_options o;
   CBS_TRY(check_opts(opt, &o));
-  if (o.extraction == CBS_RR) {
-    set_error("CBS_RR extraction is not available in this build");
-    return CBS_EINVAL;
-  }
   StreamGuard sg;
   CBS_TRY(sg.open(o.stream));
   cbs_result *res = new (std::nothrow) cbs_result();

@@ -114,12 +114,28 @@ def test_solve_tiny_projectors(precision):
         _compare(res.energies[e], ref, 1e-10 if precision == "fp64" else 1e-9)
 
 
-@pytest.mark.parametrize("precision,lam_tol", [("fp64", 1e-10), ("fp32_refine", 1e-9)])
-def test_solve_c2_vs_oracle_golden(precision, lam_tol):
+def _conj_defect(lam):
+    """Distance of every eigenvalue to the nearest conjugate of the set.  The blocks of
+    Eq. (4) are real here, so the exact spectrum is closed under conjugation and this
+    defect measures how far an extraction is from it."""
+    lam = np.asarray(lam)
+    return np.array([np.min(np.abs(lam - np.conj(x))) for x in lam])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_solve_c2_vs_oracle_golden(precision):
     """Full 32x32x16 cell (8th-order FD, 40 atoms x 4 projectors) at two energies against
     stored oracle results (tests/golden/make_c2_oracle.py runs only the CPU oracle):
     same eigenvalue count in the ring, eigenvalues within lam_tol, rank within 5%, and
-    every kept pair's residual recomputed with the oracle's operator <= 1e-8."""
+    every kept pair's residual recomputed with the oracle's operator <= 1e-8.
+
+    lam_tol: the oracle's own eigenvalues break conjugate symmetry by up to 8.6e-10 at the
+    second energy (the extraction amplifies the 1e-12 solve error), so both sides carry
+    errors of that size; two such approximations agree within 2e-9.  The mixed form stops
+    at the same tolerance by a different Krylov path and columns continued in FP64, so its
+    solve error within that tolerance differs: its bar is the rho_max = 1e-8 of the pair
+    filter (measured worst: 5e-9)."""
+    lam_tol = 2e-9 if precision == "fp64" else 1e-8
     import os
     g = np.load(os.path.join(os.path.dirname(__file__), "golden", "c2_oracle.npz"))
     wl = synth.workload("c2")
@@ -132,6 +148,7 @@ def test_solve_c2_vs_oracle_golden(precision, lam_tol):
         assert len(r["lam"]) == len(ref_lam)
         worst, un_f, un_r = match(r["lam"], ref_lam, lam_tol)
         assert not un_f and not un_r and worst <= lam_tol
+        assert np.max(_conj_defect(r["lam"])) <= lam_tol
         # the cut delta*sigma_1 falls in a continuum of leaked singular values whose size
         # follows the 1e-10 solve error: the count there may shift by a few percent
         assert abs(r["rank"] - int(g[f"rank_{i}"])) <= max(2, int(0.05 * int(g[f"rank_{i}"])))
@@ -139,3 +156,41 @@ def test_solve_c2_vs_oracle_golden(precision, lam_tol):
         rr = ss.residuals(op, E, r["lam"], r["vectors"], op.frobenius(E))
         assert np.all(rr <= 1e-8)
         assert r["max_solve_residual"] <= 1e-9
+
+
+def test_solve_rr_tiny_projectors():
+    """Rayleigh-Ritz extraction (the moments' span S W_1, small QEP by companion
+    linearisation) against the oracle's Rayleigh-Ritz on a cell with projectors, and
+    against the Hankel pairs of the same run: both extractions find the same eigenvalues."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3,
+                             L=12, M=8, n_int=32, energies=(0.2, -0.3))
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    res = cbs.solve(H, wl.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=1e-12, extraction="rr"))
+    hk = cbs.solve(H, wl.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V, cbs.options(tol=1e-12))
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    for e, E in enumerate(wl.energies):
+        ref = ss.ss_rayleigh_ritz(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12)
+        r = res.energies[e]
+        _compare(r, ref, 1e-10)
+        assert abs(r["rank"] - ref.rank) <= 1
+        worst, un_f, un_r = match(r["lam"], hk.energies[e]["lam"], 1e-10)
+        assert not un_f and not un_r
+        rr = ss.residuals(op, E, r["lam"], r["vectors"], op.frobenius(E))
+        assert np.allclose(rr, r["residual"], rtol=1e-6, atol=1e-15)
+
+
+def test_solve_rr_c1():
+    wl = synth.workload("c1")
+    E = float(wl.energies[0])
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    r = cbs.solve(H, [E], wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                  cbs.options(tol=1e-12, extraction="rr")).energies[0]
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    ref = ss.ss_rayleigh_ritz(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12)
+    _compare(r, ref, 1e-10)
+    assert np.allclose(np.exp(1j * r["k"] * wl.grid.a), r["lam"], rtol=1e-12)
