@@ -248,6 +248,10 @@ def main():
     n_e = len(energies)
     H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
     Vd = torch.from_numpy(wl.V).to(dev).contiguous()
+    # launch shapes of the stencil kernel, tuned once per cell before any timing
+    n_tune = min(64, 2 * wl.n_int * n_e)
+    tune = {"c128": cbs.autotune_apply(H, n_tune, wl.L, torch.complex128),
+            "c64": cbs.autotune_apply(H, n_tune, wl.L, torch.complex64)}
 
     def spmm(n_sys, dtype_name, iters=20):
         """Operator apply alone, at the batch shape of a step, timed with CUDA events on
@@ -322,7 +326,7 @@ def main():
     if args.spmm:
         r = spmm(args.spmm_systems or n_step_sys, args.spmm_dtype)
         if rank == 0:
-            print(json.dumps({"spmm": r, "workload": args.workload}), flush=True)
+            print(json.dumps({"spmm": r, "workload": args.workload, "apply_shape": tune}), flush=True)
         return
 
     def roofline_for(results, precision, ms_total):
@@ -386,6 +390,7 @@ def main():
     # solve, results (eigenvalues, k, residuals, eigenvectors) back to the host
     def e2e_step():
         Hh = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+        cbs.set_apply_shape(Hh, torch.complex128, tune["c128"]["py"])
         r = cbs.solve(Hh, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
                       cbs.options(precision="fp64", tol=wl.tol, delta=wl.delta))
         Hh.close()
@@ -427,7 +432,8 @@ def main():
                                    f"{n_e} energies, N_int={wl.n_int}, L={wl.L}, M={wl.M}, "
                                    f"lambda_min={wl.lambda_min}, BiCG tol {wl.tol:g}",
                        "energies_per_step": n_e, "l2": "state per step >> L2 (no flush needed)",
-                       "kept_per_energy": kept, "max_residual": worst_res, "flags": flags},
+                       "kept_per_energy": kept, "max_residual": worst_res, "flags": flags,
+                       "apply_shape": tune},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
             "cpu_baseline": cpu, "fp32_refine": mixed, "spmm": spmm_res,
             "stage_ms_last_step": {"solve": last.ms_solve, "moments": last.ms_moments,

@@ -220,13 +220,12 @@ __global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typena
   double2 wd = twist[PER_COL ? (int64_t)s * L + c : s];
   double2 wid = cdiv(make_double2(1.0, 0.0), wd);
   const C w = from_d<R>(wd), wi = from_d<R>(wid);
-  const R e = (R)E[s];
-  const R dk = (R)H.diag_kin;
-  R wx[MH + 1], wy[MH + 1], wz[MH + 1];
+  const R ed = (R)(E[s] - H.diag_kin);
+  R nwx[MH + 1], nwy[MH + 1], nwz[MH + 1];
   int ox_p[MH + 1], ox_m[MH + 1], oy_p[MH + 1], oy_m[MH + 1];
 #pragma unroll
   for (int k = 1; k <= MH; ++k) {
-    wx[k] = (R)H.wx[k]; wy[k] = (R)H.wy[k]; wz[k] = (R)H.wz[k];
+    nwx[k] = (R)-H.wx[k]; nwy[k] = (R)-H.wy[k]; nwz[k] = (R)-H.wz[k];
     ox_p[k] = (wrap_idx(ix + k, nx) - ix) * L;
     ox_m[k] = (wrap_idx(ix - k, nx) - ix) * L;
     oy_p[k] = (wrap_idx(iy + k, ny) - iy) * nx * L;
@@ -254,33 +253,48 @@ __global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typena
     q[2 * MH] = bloch(iz + MH);
     const int b = pt * L + c;
     const C x0 = q[MH];
-    const R dd = dk + vl[pt];
+    // Y = (E - d_i) x0 - sum_k w_k (pair sums) - projector part, accumulated with one
+    // FMA per pair and component (the FP64 form is bound by FP64 instruction issue)
+    const R dd = ed - vl[pt];
     C acc = mk<R>(dd * x0.x, dd * x0.y);
 #pragma unroll
     for (int k = 1; k <= MH; ++k) {
       const C a1 = Xs[b + ox_p[k]], a2 = Xs[b + ox_m[k]];
       const C b1 = Xs[b + oy_p[k]], b2 = Xs[b + oy_m[k]];
       const C z1 = q[MH + k], z2 = q[MH - k];
-      acc.x += wx[k] * (a1.x + a2.x) + wy[k] * (b1.x + b2.x) + wz[k] * (z1.x + z2.x);
-      acc.y += wx[k] * (a1.y + a2.y) + wy[k] * (b1.y + b2.y) + wz[k] * (z1.y + z2.y);
+      acc.x = fma(nwx[k], a1.x + a2.x, acc.x);
+      acc.y = fma(nwx[k], a1.y + a2.y, acc.y);
+      acc.x = fma(nwy[k], b1.x + b2.x, acc.x);
+      acc.y = fma(nwy[k], b1.y + b2.y, acc.y);
+      acc.x = fma(nwz[k], z1.x + z2.x, acc.x);
+      acc.y = fma(nwz[k], z1.y + z2.y, acc.y);
     }
     if (D) {
       for (int qq = e0; qq < e1; ++qq) {
         const int t = H.pt_ent[qq], a = H.pt_atom[qq];
         const C *Da = D + (((int64_t)s * H.n_atoms + a) * L + c) * H.np4;
-        C v = mk<R>(0, 0);
-        for (int mu = 0; mu < np; ++mu) {
-          const R p = pv[t * np + mu];
-          const C dv = Da[mu];
-          v.x += p * dv.x;
-          v.y += p * dv.y;
-        }
         const int m = H.sup_wrap[t];
-        if (m == 0) acc = cadd(acc, v);
-        else acc = cfma(m > 0 ? w : wi, v, acc);                      // w^{m} v
+        if (m == 0) {
+          for (int mu = 0; mu < np; ++mu) {
+            const R p = -pv[t * np + mu];
+            const C dv = Da[mu];
+            acc.x = fma(p, dv.x, acc.x);
+            acc.y = fma(p, dv.y, acc.y);
+          }
+        } else {
+          C v = mk<R>(0, 0);
+          for (int mu = 0; mu < np; ++mu) {
+            const R p = pv[t * np + mu];
+            const C dv = Da[mu];
+            v.x = fma(p, dv.x, v.x);
+            v.y = fma(p, dv.y, v.y);
+          }
+          const C tw = m > 0 ? w : wi;                                  // w^{m} v
+          acc = cfma(mk<R>(-tw.x, -tw.y), v, acc);
+        }
       }
     }
-    Ys[b] = mk<R>(e * x0.x - acc.x, e * x0.y - acc.y);
+    Ys[b] = acc;
 #pragma unroll
     for (int d = 0; d < 2 * MH; ++d) q[d] = q[d + 1];
   }
@@ -416,10 +430,12 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
     return CBS_EINVAL;
   }
   const typename CT<R>::T *Dp = H.n_atoms ? D : nullptr;
+  const int ti = sizeof(typename CT<R>::T) == sizeof(float2) ? 1 : 0;
   // complex64 with an even number of columns and at most 4 projectors: two columns per thread
-  if (sizeof(typename CT<R>::T) == sizeof(float2) && L % 2 == 0 && L <= 512 && H.np4 == 4) {
+  if (ti == 1 && L % 2 == 0 && L <= 512 && H.np4 == 4 && H.tune_x2 >= 0) {
     const int L2 = L / 2;
     int py = 256 / L2;
+    if (H.tune_py[1] > 0 && H.tune_py[1] * L2 <= 256) py = H.tune_py[1];
     if (py < 1) py = 1;
     dim3 blk((unsigned)L2, (unsigned)py, 1);
     dim3 grd((unsigned)ceil_div(H.nx, py), (unsigned)H.ny, (unsigned)n_sys);
@@ -446,6 +462,11 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
     return CBS_OK;
   }
   dim3 blk = col_block(L);
+  if (H.tune_py[ti] > 0 && H.tune_py[ti] * L <= 256) blk.y = (unsigned)H.tune_py[ti];
+  if (blk.x * blk.y > 256) {
+    set_error("apply: at most 256 columns per system (512 in complex64 with even L)");
+    return CBS_EINVAL;
+  }
   dim3 grd((unsigned)ceil_div(H.nx, blk.y), (unsigned)H.ny, (unsigned)n_sys);
 #define ZM(MH)                                                                                  \
   do {                                                                                          \

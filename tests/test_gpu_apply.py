@@ -10,10 +10,11 @@ from tests._gpu_common import need_gpu, rel_err, small_cases
 pytestmark = pytest.mark.gpu
 
 
-def _run(wl, zs, Es, L, dtype):
+def _run(wl, zs, Es, L, dtype, H=None):
     torch = need_gpu()
     from paper_1709_09347_gb300 import cbs
-    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    if H is None:
+        H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
     op = CellOperator(wl.grid, wl.vloc, wl.projectors)
     rng = np.random.default_rng(7)
     X = rng.standard_normal((len(zs), op.n, L)) + 1j * rng.standard_normal((len(zs), op.n, L))
@@ -51,6 +52,22 @@ def test_apply_full_size(name, L):
     wl = synth.workload(name, with_rhs=False)
     assert _run(wl, ZS[:2], ES[:2], L, "c128") < 1e-13
     assert _run(wl, ZS[:1], ES[:1], L, "c64") < 3e-6
+
+
+@pytest.mark.parametrize("name,L", [("tiny", 33), ("tiny", 12), ("c2", 32)])
+def test_autotuned_apply(name, L):
+    """cbs_autotune_apply picks a launch shape per precision; applies through the tuned
+    handle still match the oracle's operator."""
+    torch = need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = small_cases()[4] if name == "tiny" else synth.workload(name, with_rhs=False)
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    t128 = cbs.autotune_apply(H, 8, L, torch.complex128)
+    t64 = cbs.autotune_apply(H, 8, L, torch.complex64)
+    assert t128["py"] >= 1 and t128["py"] * L <= 256 and t128["ms"] > 0
+    assert t64["x2"] in ((1, -1) if L % 2 == 0 else (0,))
+    assert _run(wl, ZS, ES, L, "c128", H) < 1e-13
+    assert _run(wl, ZS, ES, L, "c64", H) < 3e-6
 
 
 @pytest.mark.parametrize("case", [0, 1, 4])
