@@ -105,6 +105,11 @@ typedef struct {
                            left are finished by FP64 BiCG (12)                             */
   int energies_per_batch; /* energies solved together; 0 = as many as fit (0)            */
   int profile;          /* 1: time every operator-apply launch with CUDA events (0)      */
+  int multi_shift;      /* 1 (CBS_FP64 only): one BiCG Krylov sequence per quadrature point
+                           and column serves every energy of a batch, since
+                           P(z, E) = P(z, E0) + (E - E0) I (shifted BiCG; not in the paper);
+                           columns whose true residual misses tol are finished by plain
+                           BiCG from the shifted solution.  0: one BiCG per system (0)     */
   void *stream;         /* cudaStream_t to run on; NULL = the library's own stream       */
 } cbs_options;
 

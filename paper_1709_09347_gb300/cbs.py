@@ -53,7 +53,8 @@ class Options(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("delta", ct.c_double), ("rho_max", ct.c_double),
                 ("max_iter", ct.c_int), ("precision", ct.c_int), ("extraction", ct.c_int),
                 ("check_every", ct.c_int), ("inner_tol", ct.c_double), ("max_sweeps", ct.c_int), ("inner_max_iter", ct.c_int), ("stall_sweeps", ct.c_int),
-                ("energies_per_batch", ct.c_int), ("profile", ct.c_int), ("stream", ct.c_void_p)]
+                ("energies_per_batch", ct.c_int), ("profile", ct.c_int), ("multi_shift", ct.c_int),
+                ("stream", ct.c_void_p)]
 
 
 class Stats(ct.Structure):

@@ -49,6 +49,7 @@ extern "C" cbs_status cbs_options_default(cbs_options *o) {
   o->inner_max_iter = 1000;
   o->stall_sweeps = 12;
   o->energies_per_batch = 0;
+  o->multi_shift = 0;
   o->stream = nullptr;
   return CBS_OK;
 }

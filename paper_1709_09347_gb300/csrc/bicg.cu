@@ -19,8 +19,15 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "bicg.cuh"
+
+#define CBS_TRY_B(x)               \
+  do {                             \
+    cbs_status _s = (x);           \
+    if (_s != CBS_OK) return _s;   \
+  } while (0)
 
 namespace cbs {
 
@@ -179,10 +186,10 @@ __global__ void k_pass_b(int n, int64_t N, int L, int chunk_pts, int n_chunks,
   if (act) {
     for (int64_t i = i0 + ly; i < i1; i += py) {
       const int64_t e = ((int64_t)s * N + i) * L + c, ed = ((int64_t)(n + s) * N + i) * L + c;
-      x[e] = cfma(a, p[e], x[e]);
+      if (x) x[e] = cfma(a, p[e], x[e]);      // no x for the seed of a shifted family
       C rr = cfma(na, q[e], r[e]);
       r[e] = rr;
-      x[ed] = cfma(ac, p[ed], x[ed]);
+      if (x) x[ed] = cfma(ac, p[ed], x[ed]);
       C rd = cfma(nac, q[ed], r[ed]);
       r[ed] = rd;
       s0 += rd.x * rr.x + rd.y * rr.y;
@@ -540,6 +547,314 @@ cbs_status Bicg<R>::replace(const double2 *R64, const int *colmask, cudaStream_t
 
 template struct Bicg<double>;
 template struct Bicg<float>;
+
+// ---------------------------------------------------------------- shifted family (MultiShift)
+__global__ void k_ms_init(int n_pt, int n_sh, int L, const int *seed_active, double2 *pi,
+                          double2 *pi_prev, double2 *alpha_prev, int *sactive, int *siters,
+                          int *sflags) {
+  const int j = blockIdx.x, c = threadIdx.x;
+  const int64_t k = (int64_t)j * L + c;
+  alpha_prev[k] = make_double2(1, 0);
+  for (int e = 0; e < n_sh; ++e) {
+    const int64_t kk = ((int64_t)e * n_pt + j) * L + c;
+    pi[kk] = make_double2(1, 0);
+    pi_prev[kk] = make_double2(1, 0);
+    sactive[kk] = seed_active[k];
+    siters[kk] = 0;
+    sflags[kk] = 0;
+  }
+}
+
+// after alpha_k: pi^{k+1} and the coefficients of this iteration for every energy
+__global__ void k_ms_coef(int n_pt, int n_sh, int L, const double *sigma, const double2 *alpha,
+                          const double2 *beta, double2 *alpha_prev, double2 *pi, double2 *pi_prev,
+                          double2 *cr, double2 *cb, double2 *ca, int *sactive, int *sflags,
+                          const int *seed_sys_active) {
+  const int j = blockIdx.x, c = threadIdx.x;
+  if (!seed_sys_active[j]) return;
+  const int64_t k = (int64_t)j * L + c;
+  const double2 a = alpha[k], b = beta[k], ap = alpha_prev[k];
+  const bool first = !(cabs2(b) > 0);
+  const double2 g = first ? make_double2(0, 0) : cdiv(cmul(a, b), ap);
+  for (int e = 0; e < n_sh; ++e) {
+    const int64_t kk = ((int64_t)e * n_pt + j) * L + c;
+    if (!sactive[kk]) {
+      cr[kk] = cb[kk] = ca[kk] = make_double2(0, 0);
+      continue;
+    }
+    const double2 pk = pi[kk], pm = pi_prev[kk];
+    const double2 f = make_double2(1.0 + a.x * sigma[e], a.y * sigma[e]);
+    const double2 pn = cadd(cmul(f, pk), cmul(g, csub(pk, pm)));
+    const double m2 = cabs2(pn);
+    if (!(m2 > 0) || !isfinite(m2)) {
+      sflags[kk] |= 2;
+      sactive[kk] = 0;
+      cr[kk] = cb[kk] = ca[kk] = make_double2(0, 0);
+      continue;
+    }
+    const double2 rk = cdiv(make_double2(1, 0), pk);
+    const double2 t = cmul(pm, rk);
+    cr[kk] = rk;
+    cb[kk] = first ? make_double2(0, 0) : cmul(cmul(t, t), b);
+    ca[kk] = cdiv(cmul(a, pk), pn);
+    pi_prev[kk] = pk;
+    pi[kk] = pn;
+  }
+  alpha_prev[k] = a;
+}
+
+// p_e = cr r + cb p_e, x_e += ca p_e (primal); conjugated coefficients for the dual.
+// One block per (chunk of points, quadrature point); every energy of that point reads the
+// same seed residual chunk.
+__global__ void k_ms_update(int n_pt, int n_sh, int64_t N, int L, int chunk_pts, const double2 *r,
+                            double2 *P, double2 *X, const double2 *cr, const double2 *cb,
+                            const double2 *ca, const int *sactive, const int *seed_sys_active) {
+  const int j = blockIdx.y, chunk = blockIdx.x, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
+  if (!seed_sys_active[j]) return;
+  const int64_t n = (int64_t)n_sh * n_pt;
+  const int64_t i0 = (int64_t)chunk * chunk_pts;
+  const int64_t i1 = min(N, i0 + chunk_pts);
+  const double2 *rp = r + (int64_t)j * N * L, *rd = r + (int64_t)(n_pt + j) * N * L;
+  for (int e = 0; e < n_sh; ++e) {
+    const int64_t s = (int64_t)e * n_pt + j;
+    const int64_t kk = s * L + c;
+    if (!sactive[kk]) continue;
+    const double2 a = cr[kk], b = cb[kk], al = ca[kk];
+    const double2 ac = cconj(a), bc = cconj(b), alc = cconj(al);
+    double2 *Pp = P + s * N * L, *Xp = X + s * N * L;
+    double2 *Pd = P + (n + s) * N * L, *Xd = X + (n + s) * N * L;
+    for (int64_t i = i0 + ly; i < i1; i += py) {
+      const int64_t o = i * L + c;
+      const double2 pv = cfma(b, Pp[o], cmul(a, rp[o]));
+      Pp[o] = pv;
+      Xp[o] = cfma(al, pv, Xp[o]);
+      const double2 pdv = cfma(bc, Pd[o], cmul(ac, rd[o]));
+      Pd[o] = pdv;
+      Xd[o] = cfma(alc, pdv, Xd[o]);
+    }
+  }
+}
+
+// seed reduction after the residual update: new rho, norms; every energy checks
+// ||r|| / |pi_e^{k+1}| (and the dual); the seed column runs while one of them is active
+__global__ void k_ms_reduce_beta(int n_pt, int n_sh, int L, int n_chunks, const double *part,
+                                 double2 *rho, double2 *rho_prev, double2 *beta, const double *tgt,
+                                 const double *tgtd, int *active, int *iters, int *flags,
+                                 int max_iter, int *sys_active, int *n_active, const double2 *pi,
+                                 int *sactive, int *siters, int *sflags) {
+  const int j = blockIdx.x, c = threadIdx.x;
+  if (!sys_active[j]) return;   // uniform per block
+  const int64_t k = (int64_t)j * L + c;
+  int act = active[k];
+  if (act) {
+    double a[4] = {0, 0, 0, 0};
+    for (int ch = 0; ch < n_chunks; ++ch)
+      for (int q = 0; q < 4; ++q) a[q] += part[(((int64_t)j * n_chunks + ch) * L + c) * 4 + q];
+    const int it = iters[k] + 1;
+    iters[k] = it;
+    const double nr = sqrt(a[2]), nrd = sqrt(a[3]);
+    const double2 rn = make_double2(a[0], a[1]);
+    const double2 rold = rho[k];
+    rho_prev[k] = rold;
+    rho[k] = rn;
+    int live = 0;
+    for (int e = 0; e < n_sh; ++e) {
+      const int64_t kk = ((int64_t)e * n_pt + j) * L + c;
+      if (!sactive[kk]) continue;
+      const double m = sqrt(cabs2(pi[kk]));
+      if (nr <= tgt[k] * m && nrd <= tgtd[k] * m) {
+        sactive[kk] = 0;
+        siters[kk] = it;
+      } else {
+        live = 1;
+      }
+    }
+    int stop_flag = 0;
+    if (!live) act = 0;
+    else if (!isfinite(nr) || !isfinite(nrd) || !(cabs2(rn) > 0)) stop_flag = 2;
+    else if (it >= max_iter) stop_flag = 1;
+    else beta[k] = cdiv(rn, rold);
+    if (stop_flag) {
+      flags[k] |= stop_flag;
+      for (int e = 0; e < n_sh; ++e) {
+        const int64_t kk = ((int64_t)e * n_pt + j) * L + c;
+        if (!sactive[kk]) continue;
+        sactive[kk] = 0;
+        siters[kk] = it;
+        sflags[kk] |= stop_flag;
+      }
+      act = 0;
+    }
+    active[k] = act;
+  }
+  if (!act) beta[k] = make_double2(0, 0);
+  int any = __syncthreads_or(act);
+  if (c == 0) {
+    sys_active[j] = any;
+    sys_active[n_pt + j] = any;
+    if (any) atomicAdd(n_active, 1);
+  }
+}
+
+size_t MultiShift::bytes_needed(const HamView &H, int n_pt, int n_sh, int L) {
+  const int64_t n = (int64_t)n_pt * n_sh;
+  int64_t b = align256(2 * n * H.n * L * (int64_t)sizeof(double2));          // P
+  b += 5 * align256(n * L * (int64_t)sizeof(double2)) + align256((int64_t)n_pt * L * sizeof(double2));
+  b += align256((int64_t)n_sh * sizeof(double)) + 3 * align256(n * L * (int64_t)sizeof(int)) + 256;
+  return (size_t)b + Bicg<double>::bytes_needed(H, n_pt, L) +
+         (size_t)align256(2 * n * H.n * L * (int64_t)sizeof(double2));         // X
+}
+
+cbs_status MultiShift::alloc(const HamView &H, int n_pt_, int n_sh_, int L_) {
+  n_pt = n_pt_; n_sh = n_sh_; L = L_; N = H.n;
+  CBS_TRY_B(seed.alloc(H, n_pt, L));
+  const int64_t n = (int64_t)n_pt * n_sh;
+  const int64_t vec = align256(2 * n * N * L * (int64_t)sizeof(double2));
+  const int64_t bytes = (int64_t)bytes_needed(H, n_pt, n_sh, L) - (int64_t)Bicg<double>::bytes_needed(H, n_pt, L) - vec;
+  if (cudaMalloc(&block, bytes) != cudaSuccess) {
+    block = nullptr;
+    set_error("cudaMalloc of the shifted-family BiCG state failed (reduce energies_per_batch)");
+    return CBS_ENOMEM;
+  }
+  if (cudaMalloc(&xblock, vec) != cudaSuccess) {
+    xblock = nullptr;
+    set_error("cudaMalloc of the shifted-family solutions failed (reduce energies_per_batch)");
+    return CBS_ENOMEM;
+  }
+  X = (double2 *)xblock;
+  char *b = (char *)block;
+  auto take = [&](int64_t sz) { char *r = b; b += align256(sz); return (void *)r; };
+  P = (double2 *)take(2 * n * N * L * (int64_t)sizeof(double2));
+  pi = (double2 *)take(n * L * (int64_t)sizeof(double2));
+  pi_prev = (double2 *)take(n * L * (int64_t)sizeof(double2));
+  cr = (double2 *)take(n * L * (int64_t)sizeof(double2));
+  cb = (double2 *)take(n * L * (int64_t)sizeof(double2));
+  ca = (double2 *)take(n * L * (int64_t)sizeof(double2));
+  alpha_prev = (double2 *)take((int64_t)n_pt * L * sizeof(double2));
+  sigma = (double *)take((int64_t)n_sh * sizeof(double));
+  sactive = (int *)take(n * L * (int64_t)sizeof(int));
+  siters = (int *)take(n * L * (int64_t)sizeof(int));
+  sflags = (int *)take(n * L * (int64_t)sizeof(int));
+  return CBS_OK;
+}
+
+void MultiShift::release() {
+  seed.release();
+  if (block) cudaFree(block);
+  block = nullptr;
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
+  exec_max_iter = exec_check_every = -1;
+}
+
+void MultiShift::release_x() {
+  if (xblock) cudaFree(xblock);
+  xblock = nullptr;
+  X = nullptr;
+}
+
+cbs_status MultiShift::init(const double2 *z1, double E0, const double *sigma_h, const double2 *B,
+                            double tol, cudaStream_t st) {
+  std::vector<double> hE(n_pt, E0);
+  CBS_CUDA(cudaMemcpyAsync(seed.E, hE.data(), n_pt * sizeof(double), cudaMemcpyHostToDevice, st));
+  CBS_TRY_B(seed.set_systems(z1, seed.E, st));   // twists and energies of the seed (and duals)
+  CBS_CUDA(cudaMemcpyAsync(sigma, sigma_h, n_sh * sizeof(double), cudaMemcpyHostToDevice, st));
+  CBS_CUDA(cudaStreamSynchronize(st));            // hE, sigma_h are host temporaries
+  CBS_TRY_B(seed.init(B, 0, B, 0, nullptr, tol, 0.0, st));
+  const int64_t n = (int64_t)n_pt * n_sh;
+  CBS_CUDA(cudaMemsetAsync(X, 0, 2 * n * N * L * sizeof(double2), st));
+  CBS_CUDA(cudaMemsetAsync(P, 0, 2 * n * N * L * sizeof(double2), st));
+  k_ms_init<<<n_pt, L, 0, st>>>(n_pt, n_sh, L, seed.active, pi, pi_prev, alpha_prev, sactive, siters,
+                                sflags); cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+cbs_status MultiShift::step(int max_iter, cudaStream_t st, int kk) {
+  Bicg<double> &b = seed;
+  dim3 blk = col_block(L);
+  dim3 grd((unsigned)b.n_chunks, (unsigned)n_pt, 1);
+  k_update_p<double><<<grd, blk, 0, st>>>(n_pt, N, L, b.chunk_pts, b.r, b.p, b.beta, b.active, b.sys_active); cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  const bool prof = b.profile && kk >= 0 && 2 * kk + 1 < b.n_prof_ev;
+  if (prof) CBS_CUDA(cudaEventRecordWithFlags(b.prof_ev[2 * kk], st, cudaEventRecordExternal));
+  cbs_status s = apply_P<double>(b.H, 2 * n_pt, L, b.p, b.q, b.tw, false, b.E, b.D, b.sys_active, st);
+  if (s != CBS_OK) return s;
+  if (prof) CBS_CUDA(cudaEventRecordWithFlags(b.prof_ev[2 * kk + 1], st, cudaEventRecordExternal));
+  k_dot_pq<double><<<grd, blk, red_smem(L), st>>>(n_pt, N, L, b.chunk_pts, b.n_chunks, b.p, b.q, b.part, b.sys_active); cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  k_reduce_alpha<<<n_pt, L, 0, st>>>(n_pt, L, b.n_chunks, b.part, b.rho, b.alpha, b.active, b.flags, b.sys_active,
+                                     b.sys_apply); cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  k_ms_coef<<<n_pt, L, 0, st>>>(n_pt, n_sh, L, sigma, b.alpha, b.beta, alpha_prev, pi, pi_prev, cr, cb, ca,
+                                sactive, sflags, b.sys_active); cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  k_ms_update<<<grd, blk, 0, st>>>(n_pt, n_sh, N, L, b.chunk_pts, b.r, P, X, cr, cb, ca, sactive, b.sys_active); cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  k_pass_b<double><<<grd, blk, red_smem(L), st>>>(n_pt, N, L, b.chunk_pts, b.n_chunks, nullptr, b.r, b.p, b.q,
+                                                  b.alpha, b.active, b.part, b.sys_active); cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  CBS_CUDA(cudaMemsetAsync(b.n_active, 0, sizeof(int), st));
+  k_ms_reduce_beta<<<n_pt, L, 0, st>>>(n_pt, n_sh, L, b.n_chunks, b.part, b.rho, b.rho_prev, b.beta, b.tgt, b.tgtd,
+                                       b.active, b.iters, b.flags, max_iter, b.sys_active, b.n_active, pi,
+                                       sactive, siters, sflags); cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  return CBS_OK;
+}
+
+cbs_status MultiShift::iterate(int max_iter, int check_every, cudaStream_t st, int *host_iters_done) {
+  Bicg<double> &b = seed;
+  if (check_every < 1) check_every = 1;
+  if (b.profile && b.n_prof_ev == 0) {
+    const int ne = 2 * (check_every < 64 ? check_every : 64);
+    for (int k = 0; k < ne; ++k) CBS_CUDA(cudaEventCreate(&b.prof_ev[k]));
+    b.n_prof_ev = ne;
+  }
+  if (!b.h_active) CBS_CUDA(cudaMallocHost(&b.h_active, sizeof(int)));
+  if (!exec || exec_max_iter != max_iter || exec_check_every != check_every) {
+    if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    const uint64_t c0 = launches_so_far();
+    CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cbs_status s = CBS_OK;
+    for (int k = 0; k < check_every && s == CBS_OK; ++k) s = step(max_iter, st, k);
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    exec_kernels = launches_so_far() - c0;
+    uncount_launches(exec_kernels);
+    if (s != CBS_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { exec = nullptr; return cuda_fail(ce, "cudaGraphInstantiate"); }
+    exec_max_iter = max_iter;
+    exec_check_every = check_every;
+  }
+  int done = 0;
+  cbs_status s = CBS_OK;
+  const int max_replays = max_iter / check_every + 2;
+  for (int rep = 0; rep < max_replays; ++rep) {
+    cudaError_t ce = cudaGraphLaunch(exec, st);
+    count_launches(exec_kernels);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(b.h_active, b.n_active, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) { s = cuda_fail(ce, "shifted-family BiCG graph replay"); break; }
+    if (b.profile) {
+      for (int k = 0; 2 * k + 1 < b.n_prof_ev && k < check_every; ++k) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, b.prof_ev[2 * k], b.prof_ev[2 * k + 1]) == cudaSuccess) {
+          b.prof_ms += ms;
+          b.prof_launches += 1;
+        } else {
+          (void)cudaGetLastError();
+        }
+      }
+    }
+    done += check_every;
+    if (*b.h_active == 0) break;
+  }
+  if (host_iters_done) *host_iters_done = done;
+  return s;
+}
 
 // ---------------------------------------------------------------- refinement helpers
 // AY holds P(z)Y (primal, systems 0..n-1) and P(z)^dagger Y~ (dual, n..2n-1); replace by

@@ -66,6 +66,45 @@ struct Bicg {
   cbs_status prof_outputs(cudaStream_t st, double *out);
 };
 
+// One BiCG Krylov sequence per (quadrature point, column) shared by a family of energies
+// (shifted BiCG; not in the paper).  For a fixed twist z, P(z, E_e) = P(z, E_0) + s_e I with
+// the real shift s_e = E_e - E_0, so the Krylov spaces of all energies coincide and the
+// BiCG residual of energy e is collinear with the seed's: r_e = r / pi_e.  With the seed's
+// alpha_k, beta_{k-1} and gamma_k = alpha_k beta_{k-1} / alpha_{k-1} (0 at k = 0):
+//     pi_e^{k+1} = (1 + alpha_k s_e) pi_e^k + gamma_k (pi_e^k - pi_e^{k-1}),  pi^0 = pi^{-1} = 1
+//     alpha_e = alpha_k pi_e^k / pi_e^{k+1},  beta_e = (pi_e^{k-1} / pi_e^k)^2 beta_{k-1}
+//     p_e = r / pi_e^k + beta_e p_e,  x_e += alpha_e p_e
+// and for the dual system (P(z, E)^dagger, E real) the same with conjugated coefficients.
+// Energy e of point j stops when ||r|| / |pi_e| and ||r~|| / |pi_e| are below tol ||b||;
+// the seed runs while any of its energies is active.  Outputs X [2n][N][L] with
+// n = n_sh * n_pt systems ordered e * n_pt + j (primal), then their duals.
+struct MultiShift {
+  Bicg<double> seed;                      // n_pt seed systems (and duals) at energy E_0
+  int n_pt = 0, n_sh = 0, L = 0;
+  int64_t N = 0;
+  double2 *X = nullptr;                   // [2n][N][L] solutions (separate allocation)
+  double2 *P = nullptr;                   // [2n][N][L] search directions of the shifts
+  double2 *pi = nullptr, *pi_prev = nullptr;            // [n][L]
+  double2 *cr = nullptr, *cb = nullptr, *ca = nullptr;  // [n][L] this iteration's coefficients
+  double2 *alpha_prev = nullptr;          // [n_pt][L]
+  double *sigma = nullptr;                // [n_sh] E_e - E_0
+  int *sactive = nullptr, *siters = nullptr, *sflags = nullptr;   // [n][L]
+  void *block = nullptr, *xblock = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int exec_max_iter = -1, exec_check_every = -1;
+  uint64_t exec_kernels = 0;
+
+  static size_t bytes_needed(const HamView &H, int n_pt, int n_sh, int L);
+  // twists z1 [n_pt] (device), shifts sigma_h [n_sh] (host) relative to E0.
+  cbs_status alloc(const HamView &H, int n_pt, int n_sh, int L);
+  cbs_status init(const double2 *z1, double E0, const double *sigma_h, const double2 *B,
+                  double tol, cudaStream_t st);
+  cbs_status step(int max_iter, cudaStream_t st, int k);
+  cbs_status iterate(int max_iter, int check_every, cudaStream_t st, int *host_iters_done);
+  void release();        // everything but X
+  void release_x();
+};
+
 // Elementwise helpers used by the refinement driver.
 // R = B - R (in place) for 2n systems, with column norms of the result into part.
 cbs_status launch_residual(int n2, int64_t N, int L, const double2 *B, int64_t bstride,

@@ -218,6 +218,84 @@ struct ShiftedSolver {
     return 2 * (4 * v16 / 2) + 2 * v16 + 2 * v16 + 2 * v16;             // f32 state, Y, R, D
   }
 
+  MultiShift ms;
+  DevBuf twbuf;
+  ~ShiftedSolver() {
+    b64.release();
+    b32.release();
+    ms.release();
+    ms.release_x();
+  }
+
+  // FP64 with one Krylov sequence per (point, column) for all n_e energies of the batch
+  // (systems ordered e * n_pt + j as in zs/Es); seed energy: the highest of the batch.
+  cbs_status run_family(const HamView &H_, int n_e, int n_pt, int L_, const double2 *z1,
+                        const double *energies_h, const double2 *zs, const double *Es,
+                        const double2 *B, const cbs_options &o, cudaStream_t st) {
+    H = H_; n = n_e * n_pt; L = L_;
+    iters.assign((size_t)n * L, 0);
+    flags.assign((size_t)n * L, 0);
+    maxrel.assign((size_t)n * L, 0.0);
+    CBS_TRY(rc.alloc(H, n, L));
+    rc.profile = o.profile != 0;
+    ms.seed.profile = b64.profile = o.profile != 0;
+    double E0 = energies_h[0];
+    for (int e = 1; e < n_e; ++e) E0 = std::max(E0, energies_h[e]);
+    std::vector<double> sig(n_e);
+    for (int e = 0; e < n_e; ++e) sig[e] = energies_h[e] - E0;
+    CBS_TRY(ms.alloc(H, n_pt, n_e, L));
+    CBS_TRY(ms.init(z1, E0, sig.data(), B, o.tol, st));
+    int done = 0;
+    CBS_TRY(ms.iterate(o.max_iter, o.check_every, st, &done));
+    Y = ms.X;
+    // twists and energies of every system for the true-residual check
+    CBS_TRY(twbuf.alloc((size_t)2 * n * (sizeof(double2) + sizeof(double)) + 256));
+    double2 *tw = twbuf.as<double2>();
+    double *E2 = (double *)(tw + 2 * n);
+    CBS_TRY(launch_twists(n, zs, Es, tw, E2, st));
+    int unconv = 0;
+    CBS_TRY(rc.run(H, Y, B, tw, E2, o.tol, st, &unconv));
+    std::vector<int> it_tmp((size_t)n * L), fl_tmp((size_t)n * L);
+    CBS_CUDA(cudaMemcpyAsync(iters.data(), ms.siters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), ms.sflags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaStreamSynchronize(st));
+    for (size_t k = 0; k < flags.size(); ++k) flags[k] |= (fl_tmp[k] & 2);
+    double oseed = 0;
+    if (o.profile) CBS_TRY(ms.seed.prof_outputs(st, &oseed));
+    const double seed_ms = ms.seed.prof_ms, seed_launches = ms.seed.prof_launches;
+    ms.release();   // keeps X (= Y)
+    if (unconv > 0) {
+      // plain FP64 BiCG on P(z) D = R, P(z)^dagger D~ = R~ for the columns left, Y += D
+      CBS_TRY(b64.alloc(H, n, L));
+      CBS_TRY(b64.set_systems(zs, Es, st));
+      CBS_TRY(b64.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
+                       rc.colmask, 0.5 * o.tol, 0.0, st, rc.bn2));
+      CBS_TRY(b64.iterate(o.tol, o.max_iter, o.check_every, st, &done));
+      CBS_TRY(launch_accumulate((int64_t)2 * n * H.n * L, Y, b64.x, st));
+      CBS_TRY(rc.run(H, Y, B, tw, E2, o.tol, st, &unconv));
+      CBS_CUDA(cudaMemcpyAsync(it_tmp.data(), b64.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), b64.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaStreamSynchronize(st));
+      for (size_t k = 0; k < iters.size(); ++k) {
+        iters[k] += it_tmp[k];
+        flags[k] |= (fl_tmp[k] & 2);
+      }
+      fp64_continued = true;
+    }
+    std::vector<int> mask((size_t)n * L);
+    CBS_CUDA(cudaMemcpyAsync(maxrel.data(), rc.maxrel, (size_t)n * L * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaMemcpyAsync(mask.data(), rc.colmask, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaStreamSynchronize(st));
+    for (size_t k = 0; k < mask.size(); ++k)
+      if (mask[k]) flags[k] |= 1;
+    sweeps = 0;
+    CBS_TRY(collect_profile(st));
+    prof_ms[CBS_C128] += seed_ms;
+    prof_launches[CBS_C128] += seed_launches;
+    prof_outputs[CBS_C128] += oseed;
+    return CBS_OK;
+  }
+
   cbs_status run(const HamView &H_, int n_, int L_, const double2 *zs, const double *Es,
                  const double2 *B, const cbs_options &o, cudaStream_t st) {
     H = H_; n = n_; L = L_;
@@ -332,7 +410,9 @@ static cbs_status check_opts(const cbs_options *opt, cbs_options *o) {
   if (!(o->tol > 0) || !(o->delta > 0) || !(o->rho_max > 0) || o->max_iter < 1 ||
       (o->precision != CBS_FP64 && o->precision != CBS_FP32_REFINE) ||
       (o->extraction != CBS_HANKEL && o->extraction != CBS_RR) || !(o->inner_tol > 0) ||
-      o->max_sweeps < 0 || o->inner_max_iter < 1 || o->stall_sweeps < 1) {
+      o->max_sweeps < 0 || o->inner_max_iter < 1 || o->stall_sweeps < 1 ||
+      (o->multi_shift != 0 && o->multi_shift != 1) ||
+      (o->multi_shift && o->precision != CBS_FP64)) {
     set_error("invalid cbs_options");
     return CBS_EINVAL;
   }
@@ -435,7 +515,10 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
     CBS_CUDA(cudaGetLastError());
     // ---- step 1: shifted solves
     ShiftedSolver S;
-    CBS_TRY(S.run(H, nsys, L, zs, Es, dV, o, st));
+    if (o.multi_shift && o.precision == CBS_FP64)
+      CBS_TRY(S.run_family(H, ne, n_int, L, z1, energies + e0, zs, Es, dV, o, st));
+    else
+      CBS_TRY(S.run(H, nsys, L, zs, Es, dV, o, st));
     for (int t = 0; t < 2; ++t) {
       res->prof_ms[t] += S.prof_ms[t];
       res->prof_launches[t] += S.prof_launches[t];
@@ -458,6 +541,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
     // free the solver state before the extraction
     S.b64.release();
     S.b32.release();
+    S.ms.release();
     // ---- step 3: extraction (Hankel SVD, reduced eigenproblem, vectors, residuals)
     const int n = nLM;   // order of the block Hankel matrices
     const size_t nn = (size_t)n * n;

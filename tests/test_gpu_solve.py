@@ -196,3 +196,53 @@ def test_solve_rr_c1():
     ref = ss.ss_rayleigh_ritz(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12)
     _compare(r, ref, 1e-10)
     assert np.allclose(np.exp(1j * r["k"] * wl.grid.a), r["lam"], rtol=1e-12)
+
+
+def test_solve_multishift_tiny():
+    """One Krylov sequence per quadrature point for all energies (shifted BiCG,
+    multi_shift = 1): moments and eigenpairs of every energy against the oracle's
+    per-energy run of Algorithm 1 (sparse solves are the definition P(z)^{-1} V)."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3,
+                             L=12, M=8, n_int=32, energies=(0.2, -0.3, 0.05))
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    res = cbs.solve(H, wl.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=1e-12, multi_shift=1))
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    for e, E in enumerate(wl.energies):
+        ref = ss.ss_hankel(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12, keep_moments=True)
+        r = res.energies[e]
+        _compare(r, ref, 1e-10)
+        assert r["max_solve_residual"] <= 1e-11
+        for k in range(2 * wl.M):
+            scale = np.max(np.abs(ref.mu[k]))
+            assert np.max(np.abs(r["mu"][k] - ref.mu[k])) <= 100 * 1e-12 * (1 / wl.lambda_min) ** (k + 1) * scale
+
+
+def test_solve_multishift_c2_vs_oracle_golden():
+    """multi_shift = 1 on the 32x32x16 cell at the two stored energies (seed: the higher
+    one): the same bars as the per-energy FP64 form."""
+    import os
+    need_gpu()
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "c2_oracle.npz"))
+    wl = synth.workload("c2")
+    idx = [int(i) for i in g["energy_index"]]
+    from paper_1709_09347_gb300 import cbs
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    res = cbs.solve(H, wl.energies[idx], wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=float(g["tol"]), multi_shift=1))
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    lam_tol = 2e-9
+    for e, i in enumerate(idx):
+        r = res.energies[e]
+        ref_lam = g[f"lam_{i}"]
+        assert len(r["lam"]) == len(ref_lam)
+        worst, un_f, un_r = match(r["lam"], ref_lam, lam_tol)
+        assert not un_f and not un_r and worst <= lam_tol
+        assert np.max(_conj_defect(r["lam"])) <= lam_tol
+        assert abs(r["rank"] - int(g[f"rank_{i}"])) <= max(2, int(0.05 * int(g[f"rank_{i}"])))
+        E = float(wl.energies[i])
+        rr = ss.residuals(op, E, r["lam"], r["vectors"], op.frobenius(E))
+        assert np.all(rr <= 1e-8)
+        assert r["max_solve_residual"] <= 1e-9
