@@ -464,7 +464,9 @@ def main():
             "cpu_baseline": cpu, "fp64_per_energy": per_energy, "fp32_refine": mixed,
             "spmm": spmm_res,
             "stage_ms_last_step": {"solve": last.ms_solve, "moments": last.ms_moments,
-                                   "extract": last.ms_extract},
+                                   "extract": last.ms_extract, "extract_svd": last.ms_svd,
+                                   "extract_reduced_eig": last.ms_reduced,
+                                   "extract_vectors": last.ms_vectors},
         }
         print(json.dumps(line), flush=True)
     if world > 1:

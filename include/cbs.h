@@ -264,6 +264,13 @@ cbs_status cbs_result_iters(const cbs_result *r, int e, int *iters);
 cbs_status cbs_result_timing(const cbs_result *r, double *ms_solve, double *ms_moments,
                              double *ms_extract, double *ms_total);
 
+/* The extraction time of cbs_result_timing split into: block Hankel matrices, SVD and rank
+ * cut (ms_svd); the reduced eigenproblem (Hankel) or nothing (Rayleigh-Ritz) (ms_reduced);
+ * per-energy vectors, Rayleigh-Ritz projection, residuals, filter and copies to the host
+ * (ms_vectors).  Milliseconds, summed over the batches of the call. */
+cbs_status cbs_result_extract_timing(const cbs_result *r, double *ms_svd, double *ms_reduced,
+                                     double *ms_vectors);
+
 /* Operator-apply (stencil + projector) launches of the last cbs_solve with profile = 1:
  * total device milliseconds, number of launches and number of complex outputs written
  * (active systems x N x L summed over launches), for element type dtype (CBS_C128 or

@@ -29,6 +29,7 @@ EXPORTS = (
     "cbs_result_timing", "cbs_result_profile", "cbs_result_free", "cbs_last_error",
     "cbs_kernel_launches", "cbs_apply_workspace_size", "cbs_apply_ws", "cbs_apply_noalloc",
     "cbs_objective", "cbs_autotune_apply", "cbs_set_apply_shape",
+    "cbs_result_extract_timing",
 )
 
 
@@ -100,6 +101,7 @@ def load():
     lib.cbs_result_moments.argtypes = [V, I, P(D)]
     lib.cbs_result_iters.argtypes = [V, I, P(I)]
     lib.cbs_result_timing.argtypes = [V, P(D), P(D), P(D), P(D)]
+    lib.cbs_result_extract_timing.argtypes = [V, P(D), P(D), P(D)]
     lib.cbs_result_profile.argtypes = [V, I, P(D), P(D), P(D)]
     lib.cbs_result_free.argtypes = [V]
     lib.cbs_result_free.restype = None
@@ -259,6 +261,9 @@ class Result:
         t = [ct.c_double() for _ in range(4)]
         _check(lib.cbs_result_timing(handle, *[ct.byref(x) for x in t]))
         self.ms_solve, self.ms_moments, self.ms_extract, self.ms_total = (x.value for x in t)
+        t = [ct.c_double() for _ in range(3)]
+        _check(lib.cbs_result_extract_timing(handle, *[ct.byref(x) for x in t]))
+        self.ms_svd, self.ms_reduced, self.ms_vectors = (x.value for x in t)
         self.profile = {}
         for name, dt in (("c128", CBS_C128), ("c64", CBS_C64)):
             a, b, c = ct.c_double(), ct.c_double(), ct.c_double()

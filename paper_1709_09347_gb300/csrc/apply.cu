@@ -34,7 +34,7 @@ template <> __device__ __forceinline__ const double *h_ptr<double>(const HamView
 template <> __device__ __forceinline__ const float *h_ptr<float>(const HamView &H) { return H.h32; }
 
 // D[s][a][mu][c] = sum_nu h_a[mu][nu] sum_{t in a} p_t[nu] w^{-m_t} X[s][i_t][c]
-template <typename R, bool PER_COL>
+template <typename R, bool PER_COL, int NPM>
 __global__ void k_proj_gather(HamView H, int L, const typename CT<R>::T *__restrict__ X,
                               const double2 *__restrict__ twist,
                               typename CT<R>::T *__restrict__ D, const int *__restrict__ sys_active) {
@@ -48,9 +48,11 @@ __global__ void k_proj_gather(HamView H, int L, const typename CT<R>::T *__restr
   double2 wd = twist[PER_COL ? (int64_t)s * L + c : s];
   double2 wid = cdiv(make_double2(1.0, 0.0), wd);
   C w = from_d<R>(wd), wi = from_d<R>(wid);
-  C acc[kMaxProj];
+  // one accumulator set per image shift m = 0, +1, -1: the twist w^{-m} is applied once
+  // per column at the end instead of once per support entry
+  C acc[NPM], accp[NPM], accm[NPM];
 #pragma unroll
-  for (int mu = 0; mu < kMaxProj; ++mu) acc[mu] = mk<R>(0, 0);
+  for (int mu = 0; mu < NPM; ++mu) acc[mu] = accp[mu] = accm[mu] = mk<R>(0, 0);
   const R *pv = pval_ptr<R>(H);
   const int64_t t0 = H.sup_ptr[a], t1 = H.sup_ptr[a + 1];
   const C *Xs = X + (int64_t)s * H.n * L;
@@ -74,33 +76,62 @@ __global__ void k_proj_gather(HamView H, int L, const typename CT<R>::T *__restr
     for (int u = 0; u < U; ++u) {
       const int64_t t = tb + (int64_t)u * py;
       if (t >= t1) break;
-      const C f = (mw[u] == 0) ? xv[u] : (mw[u] > 0 ? cmul(wi, xv[u]) : cmul(w, xv[u]));  // w^{-m} x
+      const C f = xv[u];
+      if (mw[u] == 0) {
 #pragma unroll
-      for (int mu = 0; mu < kMaxProj; ++mu)
-        if (mu < np) {
-          const R p = pv[t * np + mu];
-          acc[mu].x += p * f.x;
-          acc[mu].y += p * f.y;
-        }
+        for (int mu = 0; mu < NPM; ++mu)
+          if (mu < np) {
+            const R p = pv[t * np + mu];
+            acc[mu].x = fma(p, f.x, acc[mu].x);
+            acc[mu].y = fma(p, f.y, acc[mu].y);
+          }
+      } else if (mw[u] > 0) {
+#pragma unroll
+        for (int mu = 0; mu < NPM; ++mu)
+          if (mu < np) {
+            const R p = pv[t * np + mu];
+            accp[mu].x = fma(p, f.x, accp[mu].x);
+            accp[mu].y = fma(p, f.y, accp[mu].y);
+          }
+      } else {
+#pragma unroll
+        for (int mu = 0; mu < NPM; ++mu)
+          if (mu < np) {
+            const R p = pv[t * np + mu];
+            accm[mu].x = fma(p, f.x, accm[mu].x);
+            accm[mu].y = fma(p, f.y, accm[mu].y);
+          }
+      }
     }
   }
-  for (int mu = 0; mu < np; ++mu) red[((int64_t)ly * np + mu) * L + c] = acc[mu];
+#pragma unroll
+  for (int mu = 0; mu < NPM; ++mu)                      // w^{-m} for m = +1, -1
+    acc[mu] = cadd(acc[mu], cadd(cmul(wi, accp[mu]), cmul(w, accm[mu])));
+#pragma unroll
+  for (int mu = 0; mu < NPM; ++mu)
+    if (mu < np) red[((int64_t)ly * np + mu) * L + c] = acc[mu];
   __syncthreads();
   if (ly == 0) {
-    C cc[kMaxProj];
-    for (int mu = 0; mu < np; ++mu) {
+    C cc[NPM];
+#pragma unroll
+    for (int mu = 0; mu < NPM; ++mu) {
       C sum = mk<R>(0, 0);
-      for (int y = 0; y < py; ++y) sum = cadd(sum, red[((int64_t)y * np + mu) * L + c]);
+      if (mu < np)
+        for (int y = 0; y < py; ++y) sum = cadd(sum, red[((int64_t)y * np + mu) * L + c]);
       cc[mu] = sum;
     }
     const R *ha = h_ptr<R>(H) + (int64_t)a * np * np;
-    for (int mu = 0; mu < np; ++mu) {
+#pragma unroll
+    for (int mu = 0; mu < NPM; ++mu) {
+      if (mu >= np) break;
       C d = mk<R>(0, 0);
-      for (int nu = 0; nu < np; ++nu) {
-        R hv = ha[mu * np + nu];
-        d.x += hv * cc[nu].x;
-        d.y += hv * cc[nu].y;
-      }
+#pragma unroll
+      for (int nu = 0; nu < NPM; ++nu)
+        if (nu < np) {
+          R hv = ha[mu * np + nu];
+          d.x += hv * cc[nu].x;
+          d.y += hv * cc[nu].y;
+        }
       D[(((int64_t)s * H.n_atoms + a) * L + c) * H.np4 + mu] = d;
     }
     for (int mu = np; mu < H.np4; ++mu) D[(((int64_t)s * H.n_atoms + a) * L + c) * H.np4 + mu] = mk<R>(0, 0);
@@ -411,10 +442,13 @@ cbs_status launch_proj_gather(const HamView &H, int n_sys, int L, const typename
     CBS_CUDA(cudaGetLastError());
     return CBS_OK;
   }
-  if (per_col)
-    k_proj_gather<R, true><<<grd, blk, sm, st>>>(H, L, X, twist, D, sys_active);
-  else
-    k_proj_gather<R, false><<<grd, blk, sm, st>>>(H, L, X, twist, D, sys_active);
+  if (H.n_proj <= 4) {
+    if (per_col) k_proj_gather<R, true, 4><<<grd, blk, sm, st>>>(H, L, X, twist, D, sys_active);
+    else k_proj_gather<R, false, 4><<<grd, blk, sm, st>>>(H, L, X, twist, D, sys_active);
+  } else {
+    if (per_col) k_proj_gather<R, true, kMaxProj><<<grd, blk, sm, st>>>(H, L, X, twist, D, sys_active);
+    else k_proj_gather<R, false, kMaxProj><<<grd, blk, sm, st>>>(H, L, X, twist, D, sys_active);
+  }
   cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;

@@ -568,7 +568,7 @@ __global__ void k_ms_init(int n_pt, int n_sh, int L, const int *seed_active, dou
 // after alpha_k: pi^{k+1} and the coefficients of this iteration for every energy
 __global__ void k_ms_coef(int n_pt, int n_sh, int L, const double *sigma, const double2 *alpha,
                           const double2 *beta, double2 *alpha_prev, double2 *pi, double2 *pi_prev,
-                          double2 *cr, double2 *cb, double2 *ca, int *sactive, int *sflags,
+                          double2 *cb, double2 *ca, int *sactive, int *sflags,
                           const int *seed_sys_active) {
   const int j = blockIdx.x, c = threadIdx.x;
   if (!seed_sys_active[j]) return;
@@ -579,7 +579,7 @@ __global__ void k_ms_coef(int n_pt, int n_sh, int L, const double *sigma, const 
   for (int e = 0; e < n_sh; ++e) {
     const int64_t kk = ((int64_t)e * n_pt + j) * L + c;
     if (!sactive[kk]) {
-      cr[kk] = cb[kk] = ca[kk] = make_double2(0, 0);
+      cb[kk] = ca[kk] = make_double2(0, 0);
       continue;
     }
     const double2 pk = pi[kk], pm = pi_prev[kk];
@@ -589,25 +589,24 @@ __global__ void k_ms_coef(int n_pt, int n_sh, int L, const double *sigma, const 
     if (!(m2 > 0) || !isfinite(m2)) {
       sflags[kk] |= 2;
       sactive[kk] = 0;
-      cr[kk] = cb[kk] = ca[kk] = make_double2(0, 0);
+      cb[kk] = ca[kk] = make_double2(0, 0);
       continue;
     }
-    const double2 rk = cdiv(make_double2(1, 0), pk);
-    const double2 t = cmul(pm, rk);
-    cr[kk] = rk;
-    cb[kk] = first ? make_double2(0, 0) : cmul(cmul(t, t), b);
-    ca[kk] = cdiv(cmul(a, pk), pn);
+    // the kernel keeps p^_e = pi_e^k p_e: p^_e = r + (pi_e^{k-1} / pi_e^k) beta_{k-1} p^_e,
+    // x_e += (alpha_k / pi_e^{k+1}) p^_e  (4 FP64 FMA each per component pair)
+    cb[kk] = first ? make_double2(0, 0) : cmul(cdiv(pm, pk), b);
+    ca[kk] = cdiv(a, pn);
     pi_prev[kk] = pk;
     pi[kk] = pn;
   }
   alpha_prev[k] = a;
 }
 
-// p_e = cr r + cb p_e, x_e += ca p_e (primal); conjugated coefficients for the dual.
-// One block per (chunk of points, quadrature point); every energy of that point reads the
-// same seed residual chunk.
+// p^_e = r + cb p^_e, x_e += ca p^_e (primal; p^_e = pi_e^k p_e, the scaled search
+// direction); conjugated coefficients for the dual.  One block per (chunk of points,
+// quadrature point); every energy of that point reads the same seed residual chunk.
 __global__ void k_ms_update(int n_pt, int n_sh, int64_t N, int L, int chunk_pts, const double2 *r,
-                            double2 *P, double2 *X, const double2 *cr, const double2 *cb,
+                            double2 *P, double2 *X, const double2 *cb,
                             const double2 *ca, const int *sactive, const int *seed_sys_active) {
   const int j = blockIdx.y, chunk = blockIdx.x, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
   if (!seed_sys_active[j]) return;
@@ -619,16 +618,16 @@ __global__ void k_ms_update(int n_pt, int n_sh, int64_t N, int L, int chunk_pts,
     const int64_t s = (int64_t)e * n_pt + j;
     const int64_t kk = s * L + c;
     if (!sactive[kk]) continue;
-    const double2 a = cr[kk], b = cb[kk], al = ca[kk];
-    const double2 ac = cconj(a), bc = cconj(b), alc = cconj(al);
+    const double2 b = cb[kk], al = ca[kk];
+    const double2 bc = cconj(b), alc = cconj(al);
     double2 *Pp = P + s * N * L, *Xp = X + s * N * L;
     double2 *Pd = P + (n + s) * N * L, *Xd = X + (n + s) * N * L;
     for (int64_t i = i0 + ly; i < i1; i += py) {
       const int64_t o = i * L + c;
-      const double2 pv = cfma(b, Pp[o], cmul(a, rp[o]));
+      const double2 pv = cfma(b, Pp[o], rp[o]);
       Pp[o] = pv;
       Xp[o] = cfma(al, pv, Xp[o]);
-      const double2 pdv = cfma(bc, Pd[o], cmul(ac, rd[o]));
+      const double2 pdv = cfma(bc, Pd[o], rd[o]);
       Pd[o] = pdv;
       Xd[o] = cfma(alc, pdv, Xd[o]);
     }
@@ -699,7 +698,7 @@ __global__ void k_ms_reduce_beta(int n_pt, int n_sh, int L, int n_chunks, const 
 size_t MultiShift::bytes_needed(const HamView &H, int n_pt, int n_sh, int L) {
   const int64_t n = (int64_t)n_pt * n_sh;
   int64_t b = align256(2 * n * H.n * L * (int64_t)sizeof(double2));          // P
-  b += 5 * align256(n * L * (int64_t)sizeof(double2)) + align256((int64_t)n_pt * L * sizeof(double2));
+  b += 4 * align256(n * L * (int64_t)sizeof(double2)) + align256((int64_t)n_pt * L * sizeof(double2));
   b += align256((int64_t)n_sh * sizeof(double)) + 3 * align256(n * L * (int64_t)sizeof(int)) + 256;
   return (size_t)b + Bicg<double>::bytes_needed(H, n_pt, L) +
          (size_t)align256(2 * n * H.n * L * (int64_t)sizeof(double2));         // X
@@ -727,7 +726,6 @@ cbs_status MultiShift::alloc(const HamView &H, int n_pt_, int n_sh_, int L_) {
   P = (double2 *)take(2 * n * N * L * (int64_t)sizeof(double2));
   pi = (double2 *)take(n * L * (int64_t)sizeof(double2));
   pi_prev = (double2 *)take(n * L * (int64_t)sizeof(double2));
-  cr = (double2 *)take(n * L * (int64_t)sizeof(double2));
   cb = (double2 *)take(n * L * (int64_t)sizeof(double2));
   ca = (double2 *)take(n * L * (int64_t)sizeof(double2));
   alpha_prev = (double2 *)take((int64_t)n_pt * L * sizeof(double2));
@@ -786,10 +784,10 @@ cbs_status MultiShift::step(int max_iter, cudaStream_t st, int kk) {
   k_reduce_alpha<<<n_pt, L, 0, st>>>(n_pt, L, b.n_chunks, b.part, b.rho, b.alpha, b.active, b.flags, b.sys_active,
                                      b.sys_apply); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
-  k_ms_coef<<<n_pt, L, 0, st>>>(n_pt, n_sh, L, sigma, b.alpha, b.beta, alpha_prev, pi, pi_prev, cr, cb, ca,
+  k_ms_coef<<<n_pt, L, 0, st>>>(n_pt, n_sh, L, sigma, b.alpha, b.beta, alpha_prev, pi, pi_prev, cb, ca,
                                 sactive, sflags, b.sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
-  k_ms_update<<<grd, blk, 0, st>>>(n_pt, n_sh, N, L, b.chunk_pts, b.r, P, X, cr, cb, ca, sactive, b.sys_active); cbs::count_launches(1);
+  k_ms_update<<<grd, blk, 0, st>>>(n_pt, n_sh, N, L, b.chunk_pts, b.r, P, X, cb, ca, sactive, b.sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   k_pass_b<double><<<grd, blk, red_smem(L), st>>>(n_pt, N, L, b.chunk_pts, b.n_chunks, nullptr, b.r, b.p, b.q,
                                                   b.alpha, b.active, b.part, b.sys_active); cbs::count_launches(1);

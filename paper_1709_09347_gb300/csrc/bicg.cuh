@@ -75,6 +75,8 @@ struct Bicg {
 //     alpha_e = alpha_k pi_e^k / pi_e^{k+1},  beta_e = (pi_e^{k-1} / pi_e^k)^2 beta_{k-1}
 //     p_e = r / pi_e^k + beta_e p_e,  x_e += alpha_e p_e
 // and for the dual system (P(z, E)^dagger, E real) the same with conjugated coefficients.
+// The directions are stored scaled, p^_e = pi_e^k p_e, which turns the update into
+// p^_e = r + (pi_e^{k-1}/pi_e^k) beta_{k-1} p^_e and x_e += (alpha_k / pi_e^{k+1}) p^_e.
 // Energy e of point j stops when ||r|| / |pi_e| and ||r~|| / |pi_e| are below tol ||b||;
 // the seed runs while any of its energies is active.  Outputs X [2n][N][L] with
 // n = n_sh * n_pt systems ordered e * n_pt + j (primal), then their duals.
@@ -83,9 +85,9 @@ struct MultiShift {
   int n_pt = 0, n_sh = 0, L = 0;
   int64_t N = 0;
   double2 *X = nullptr;                   // [2n][N][L] solutions (separate allocation)
-  double2 *P = nullptr;                   // [2n][N][L] search directions of the shifts
+  double2 *P = nullptr;                   // [2n][N][L] scaled search directions pi_e p_e
   double2 *pi = nullptr, *pi_prev = nullptr;            // [n][L]
-  double2 *cr = nullptr, *cb = nullptr, *ca = nullptr;  // [n][L] this iteration's coefficients
+  double2 *cb = nullptr, *ca = nullptr;  // [n][L] this iteration's coefficients
   double2 *alpha_prev = nullptr;          // [n_pt][L]
   double *sigma = nullptr;                // [n_sh] E_e - E_0
   int *sactive = nullptr, *siters = nullptr, *sflags = nullptr;   // [n][L]

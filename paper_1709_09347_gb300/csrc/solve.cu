@@ -29,6 +29,7 @@ struct cbs_result {
   int64_t N = 0;
   std::vector<cbs_energy_result> e;
   double ms_solve = 0, ms_moments = 0, ms_extract = 0, ms_total = 0;
+  double ms_svd = 0, ms_reduced = 0, ms_vectors = 0;   // parts of ms_extract
   double prof_ms[2] = {0, 0}, prof_launches[2] = {0, 0}, prof_outputs[2] = {0, 0};
 };
 
@@ -562,6 +563,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
     CBS_CUDA(cudaMemcpyAsync(Aw, T, nn * ne * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     CBS_TRY(launch_svd(ne, n, Aw, Ww, U, Ws, sig, isvd, st));
     CBS_TRY(launch_rank(ne, n, sig, o.delta, mhat, st));
+    CBS_TRY(lap(&res->ms_svd));
     const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
     // C1 = T^< W (all n columns), Bm = U^dagger C1, then columns j < m_hat scaled by 1/sigma_j
     if (o.extraction == CBS_HANKEL) {
@@ -572,6 +574,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
     } else {
       CBS_CUDA(cudaMemsetAsync(small + ne, 0, (size_t)3 * ne * sizeof(int), st));
     }
+    CBS_TRY(lap(&res->ms_reduced));
     std::vector<int> hsmall(4 * ne);
     std::vector<double> hsig((size_t)ne * n);
     std::vector<double2> htau((size_t)ne * n);
@@ -709,8 +712,9 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
         CBS_TRY(finish(cnt, Psi, twr, hridx.data()));
       }
     }
-    CBS_TRY(lap(&res->ms_extract));
+    CBS_TRY(lap(&res->ms_vectors));
   }
+  res->ms_extract = res->ms_svd + res->ms_reduced + res->ms_vectors;
   res->ms_total = res->ms_solve + res->ms_moments + res->ms_extract;
   return ret;
 }
@@ -785,6 +789,15 @@ extern "C" cbs_status cbs_result_moments(const cbs_result *r, int e, double *mu)
 extern "C" cbs_status cbs_result_iters(const cbs_result *r, int e, int *iters) {
   if (!r || e < 0 || e >= r->n_e || !iters) { set_error("bad result/energy index"); return CBS_EINVAL; }
   memcpy(iters, r->e[e].iters.data(), r->e[e].iters.size() * sizeof(int));
+  return CBS_OK;
+}
+
+extern "C" cbs_status cbs_result_extract_timing(const cbs_result *r, double *ms_svd,
+                                                double *ms_reduced, double *ms_vectors) {
+  if (!r) { set_error("null result"); return CBS_EINVAL; }
+  if (ms_svd) *ms_svd = r->ms_svd;
+  if (ms_reduced) *ms_reduced = r->ms_reduced;
+  if (ms_vectors) *ms_vectors = r->ms_vectors;
   return CBS_OK;
 }
 
