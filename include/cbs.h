@@ -274,7 +274,10 @@ cbs_status cbs_result_extract_timing(const cbs_result *r, double *ms_svd, double
 /* Operator-apply (stencil + projector) launches of the last cbs_solve with profile = 1:
  * total device milliseconds, number of launches and number of complex outputs written
  * (active systems x N x L summed over launches), for element type dtype (CBS_C128 or
- * CBS_C64).  All zero when profiling was off. */
+ * CBS_C64).  dtype = CBS_PROFILE_SHIFT_UPDATE instead reports the update kernel of the
+ * shifted family (multi_shift = 1): milliseconds, launches and the grid points x active
+ * (energy, point, column) triples it updated.  All zero when profiling was off. */
+enum { CBS_PROFILE_SHIFT_UPDATE = 2 };
 cbs_status cbs_result_profile(const cbs_result *r, int dtype, double *ms, double *launches,
                               double *outputs);
 

@@ -265,7 +265,7 @@ class Result:
         _check(lib.cbs_result_extract_timing(handle, *[ct.byref(x) for x in t]))
         self.ms_svd, self.ms_reduced, self.ms_vectors = (x.value for x in t)
         self.profile = {}
-        for name, dt in (("c128", CBS_C128), ("c64", CBS_C64)):
+        for name, dt in (("c128", CBS_C128), ("c64", CBS_C64), ("shift_update", 2)):
             a, b, c = ct.c_double(), ct.c_double(), ct.c_double()
             _check(lib.cbs_result_profile(handle, dt, ct.byref(a), ct.byref(b), ct.byref(c)))
             self.profile[name] = dict(ms=a.value, launches=b.value, outputs=c.value)

@@ -569,9 +569,10 @@ __global__ void k_ms_init(int n_pt, int n_sh, int L, const int *seed_active, dou
 __global__ void k_ms_coef(int n_pt, int n_sh, int L, const double *sigma, const double2 *alpha,
                           const double2 *beta, double2 *alpha_prev, double2 *pi, double2 *pi_prev,
                           double2 *cb, double2 *ca, int *sactive, int *sflags,
-                          const int *seed_sys_active) {
+                          const int *seed_sys_active, unsigned long long *upd_cols) {
   const int j = blockIdx.x, c = threadIdx.x;
   if (!seed_sys_active[j]) return;
+  int live = 0;
   const int64_t k = (int64_t)j * L + c;
   const double2 a = alpha[k], b = beta[k], ap = alpha_prev[k];
   const bool first = !(cabs2(b) > 0);
@@ -598,8 +599,13 @@ __global__ void k_ms_coef(int n_pt, int n_sh, int L, const double *sigma, const 
     ca[kk] = cdiv(a, pn);
     pi_prev[kk] = pk;
     pi[kk] = pn;
+    ++live;
   }
   alpha_prev[k] = a;
+  if (upd_cols) {
+    for (int o = 16; o > 0; o >>= 1) live += __shfl_xor_sync(0xffffffffu, live, o);
+    if ((c & 31) == 0 && live) atomicAdd(upd_cols, (unsigned long long)live);
+  }
 }
 
 // p^_e = r + cb p^_e, x_e += ca p^_e (primal; p^_e = pi_e^k p_e, the scaled search
@@ -699,7 +705,7 @@ size_t MultiShift::bytes_needed(const HamView &H, int n_pt, int n_sh, int L) {
   const int64_t n = (int64_t)n_pt * n_sh;
   int64_t b = align256(2 * n * H.n * L * (int64_t)sizeof(double2));          // P
   b += 4 * align256(n * L * (int64_t)sizeof(double2)) + align256((int64_t)n_pt * L * sizeof(double2));
-  b += align256((int64_t)n_sh * sizeof(double)) + 3 * align256(n * L * (int64_t)sizeof(int)) + 256;
+  b += align256((int64_t)n_sh * sizeof(double)) + 3 * align256(n * L * (int64_t)sizeof(int)) + 512;
   return (size_t)b + Bicg<double>::bytes_needed(H, n_pt, L) +
          (size_t)align256(2 * n * H.n * L * (int64_t)sizeof(double2));         // X
 }
@@ -733,11 +739,23 @@ cbs_status MultiShift::alloc(const HamView &H, int n_pt_, int n_sh_, int L_) {
   sactive = (int *)take(n * L * (int64_t)sizeof(int));
   siters = (int *)take(n * L * (int64_t)sizeof(int));
   sflags = (int *)take(n * L * (int64_t)sizeof(int));
+  upd_cols = (unsigned long long *)take(256);
+  CBS_CUDA(cudaMemset(upd_cols, 0, sizeof(unsigned long long)));
+  return CBS_OK;
+}
+
+cbs_status MultiShift::update_columns(cudaStream_t st, double *out) {
+  unsigned long long v = 0;
+  CBS_CUDA(cudaMemcpyAsync(&v, upd_cols, sizeof(v), cudaMemcpyDeviceToHost, st));
+  CBS_CUDA(cudaStreamSynchronize(st));
+  *out = (double)v;
   return CBS_OK;
 }
 
 void MultiShift::release() {
   seed.release();
+  for (int k = 0; k < n_upd_ev; ++k) cudaEventDestroy(upd_ev[k]);
+  n_upd_ev = 0;
   if (block) cudaFree(block);
   block = nullptr;
   if (exec) cudaGraphExecDestroy(exec);
@@ -785,10 +803,13 @@ cbs_status MultiShift::step(int max_iter, cudaStream_t st, int kk) {
                                      b.sys_apply); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   k_ms_coef<<<n_pt, L, 0, st>>>(n_pt, n_sh, L, sigma, b.alpha, b.beta, alpha_prev, pi, pi_prev, cb, ca,
-                                sactive, sflags, b.sys_active); cbs::count_launches(1);
+                                sactive, sflags, b.sys_active, b.profile ? upd_cols : nullptr); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
+  const bool uprof = b.profile && kk >= 0 && 2 * kk + 1 < n_upd_ev;
+  if (uprof) CBS_CUDA(cudaEventRecordWithFlags(upd_ev[2 * kk], st, cudaEventRecordExternal));
   k_ms_update<<<grd, blk, 0, st>>>(n_pt, n_sh, N, L, b.chunk_pts, b.r, P, X, cb, ca, sactive, b.sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
+  if (uprof) CBS_CUDA(cudaEventRecordWithFlags(upd_ev[2 * kk + 1], st, cudaEventRecordExternal));
   k_pass_b<double><<<grd, blk, red_smem(L), st>>>(n_pt, N, L, b.chunk_pts, b.n_chunks, nullptr, b.r, b.p, b.q,
                                                   b.alpha, b.active, b.part, b.sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
@@ -807,6 +828,8 @@ cbs_status MultiShift::iterate(int max_iter, int check_every, cudaStream_t st, i
     const int ne = 2 * (check_every < 64 ? check_every : 64);
     for (int k = 0; k < ne; ++k) CBS_CUDA(cudaEventCreate(&b.prof_ev[k]));
     b.n_prof_ev = ne;
+    for (int k = 0; k < ne; ++k) CBS_CUDA(cudaEventCreate(&upd_ev[k]));
+    n_upd_ev = ne;
   }
   if (!b.h_active) CBS_CUDA(cudaMallocHost(&b.h_active, sizeof(int)));
   if (!exec || exec_max_iter != max_iter || exec_check_every != check_every) {
@@ -842,6 +865,13 @@ cbs_status MultiShift::iterate(int max_iter, int check_every, cudaStream_t st, i
         if (cudaEventElapsedTime(&ms, b.prof_ev[2 * k], b.prof_ev[2 * k + 1]) == cudaSuccess) {
           b.prof_ms += ms;
           b.prof_launches += 1;
+        } else {
+          (void)cudaGetLastError();
+        }
+        if (2 * k + 1 < n_upd_ev &&
+            cudaEventElapsedTime(&ms, upd_ev[2 * k], upd_ev[2 * k + 1]) == cudaSuccess) {
+          upd_ms += ms;
+          upd_launches += 1;
         } else {
           (void)cudaGetLastError();
         }

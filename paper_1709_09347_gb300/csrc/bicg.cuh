@@ -95,8 +95,15 @@ struct MultiShift {
   cudaGraphExec_t exec = nullptr;
   int exec_max_iter = -1, exec_check_every = -1;
   uint64_t exec_kernels = 0;
+  // profiling of the update kernel (events around each launch inside the graph) and the
+  // number of active (energy, point, column) triples it processed
+  cudaEvent_t upd_ev[2 * 64] = {};
+  int n_upd_ev = 0;
+  double upd_ms = 0, upd_launches = 0;
+  unsigned long long *upd_cols = nullptr;
 
   static size_t bytes_needed(const HamView &H, int n_pt, int n_sh, int L);
+  cbs_status update_columns(cudaStream_t st, double *out);
   // twists z1 [n_pt] (device), shifts sigma_h [n_sh] (host) relative to E0.
   cbs_status alloc(const HamView &H, int n_pt, int n_sh, int L);
   cbs_status init(const double2 *z1, double E0, const double *sigma_h, const double2 *B,

@@ -281,6 +281,7 @@ __global__ void k_scale_cols(int n, int ldm, const int *mhat, const double *sig,
 // eigenvalues (those strictly inside the ring), compacted into Yc (m x n_ring) and
 // transformed by Z outside this kernel.
 constexpr int kEigThreads = 512;
+constexpr int kMaxEigN = 512;   // largest eigenproblem (launch_eig rejects larger)
 // shift: 0 selects eigenvalues tau inside the ring; otherwise the eigenvalues are mu of a
 // shifted-and-inverted problem, lambda = shift + 1/mu is tested and written back to tau.
 __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, double2 *Bb, double2 *Zb,
@@ -351,12 +352,33 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
     __syncthreads();
   }
   // ---- shifted QR (single shift, Wilkinson; exceptional shifts every 10 stalls)
+  // Each sweep chases the bulge through the active window [l, hi] only: a rotation updates
+  // rows k, k+1 for columns up to hi and columns k, k+1 for rows from l.  The parts outside
+  // the window (rows k, k+1 right of hi, columns k, k+1 above l) and the Schur vectors Z are
+  // not read by the chase; they receive the sweep's rotations afterwards in one parallel
+  // pass, each thread applying them in order to its own column or row (the same operations
+  // per element, in the same order).  The next rotation's inputs pass through a
+  // double-buffered shared slot, so a rotation needs two block barriers.
   const double eps = 2.220446049250313e-16;
+  __shared__ double rot_c[kMaxEigN];
+  __shared__ double2 rot_s[kMaxEigN];
+  __shared__ double2 nx[2], ny[2];
+  __shared__ int sh_defl[kEigThreads / 32];
   if (tid == 0) { sh_hi = m - 1; sh_fail = 0; }
   __syncthreads();
   int its = 0, total = 0;
   while (true) {
-    __syncthreads();   // everyone has read the previous decision
+    // deflation: the largest l <= hi with a negligible subdiagonal entry (0 if none)
+    const int hi0 = sh_hi;
+    int best = 0;
+    for (int q = 1 + tid; q <= hi0; q += nt) {
+      double sc = cabs1(Aat(q - 1, q - 1)) + cabs1(Aat(q, q));
+      if (sc == 0) sc = 1e-300;
+      if (cabs1(Aat(q, q - 1)) <= eps * sc) best = max(best, q);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((tid & 31) == 0) sh_defl[tid >> 5] = best;
+    __syncthreads();
     if (tid == 0) {
       int hi = sh_hi;
       sh_act = 0;
@@ -366,12 +388,9 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
         tau[0] = Aat(0, 0);
         sh_hi = -1;
       } else {
-        int l = hi;
-        for (; l > 0; --l) {
-          double s = cabs1(Aat(l - 1, l - 1)) + cabs1(Aat(l, l));
-          if (s == 0) s = 1e-300;
-          if (cabs1(Aat(l, l - 1)) <= eps * s) { Aat(l, l - 1) = make_double2(0, 0); break; }
-        }
+        int l = 0;
+        for (int w = 0; w < nt / 32; ++w) l = max(l, sh_defl[w]);
+        if (l > 0) Aat(l, l - 1) = make_double2(0, 0);
         if (l == hi) {
           tau[hi] = Aat(hi, hi);
           sh_hi = hi - 1;
@@ -397,6 +416,8 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
           sh_mu = mu;
           sh_l = l;
           sh_act = 1;
+          nx[0] = csub(Aat(l, l), mu);
+          ny[0] = Aat(l + 1, l);
         }
       }
     }
@@ -405,46 +426,77 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
     if (act < 0) break;
     if (act == 0) continue;
     const int l = sh_l, hi = sh_hi;
-    const double2 mu = sh_mu;
     for (int k = l; k < hi; ++k) {
-      double2 x, y;
-      if (k == l) { x = csub(Aat(l, l), mu); y = Aat(l + 1, l); }
-      else { x = Aat(k, k - 1); y = Aat(k + 1, k - 1); }
+      const double2 x = nx[(k - l) & 1], y = ny[(k - l) & 1];
       const double ax = cabsd(x), ay = cabsd(y);
       const double rho = hypot(ax, ay);
       double c;
-      double2 s;
-      if (rho == 0) { c = 1; s = make_double2(0, 0); }
-      else if (ax == 0) { c = 0; s = make_double2(y.x / ay, -y.y / ay); }   // conj(y)/|y|
+      double2 sr;
+      if (rho == 0) { c = 1; sr = make_double2(0, 0); }
+      else if (ax == 0) { c = 0; sr = make_double2(y.x / ay, -y.y / ay); }   // conj(y)/|y|
       else {
         c = ax / rho;
         const double2 phx = make_double2(x.x / ax, x.y / ax);
-        s = cscale(cmul(phx, cconj(y)), 1.0 / rho);
+        sr = cscale(cmul(phx, cconj(y)), 1.0 / rho);
       }
-      __syncthreads();
-      // rows k, k+1:  [a; b] <- [c a + s b; -conj(s) a + c b]
+      if (tid == 0) { rot_c[k] = c; rot_s[k] = sr; }
+      // rows k, k+1 inside the window:  [a; b] <- [c a + s b; -conj(s) a + c b]
       const int j0 = (k == l) ? l : k - 1;
-      for (int j = j0 + tid; j < m; j += nt) {
+      for (int j = j0 + tid; j <= hi; j += nt) {
         const double2 a = Aat(k, j), b = Aat(k + 1, j);
-        Aat(k, j) = cadd(cscale(a, c), cmul(s, b));
-        Aat(k + 1, j) = csub(cscale(b, c), cmul(cconj(s), a));
+        Aat(k, j) = cadd(cscale(a, c), cmul(sr, b));
+        Aat(k + 1, j) = csub(cscale(b, c), cmul(cconj(sr), a));
       }
       __syncthreads();
       if (k > l && tid == 0) Aat(k + 1, k - 1) = make_double2(0, 0);
-      // columns k, k+1:  [u, w] <- [c u + conj(s) w, -s u + c w]
+      // columns k, k+1 inside the window:  [u, w] <- [c u + conj(s) w, -s u + c w]
       const int i1 = min(k + 2, hi);
-      for (int i = tid; i <= i1; i += nt) {
+      for (int i = l + tid; i <= i1; i += nt) {
         const double2 u = Aat(i, k), w = Aat(i, k + 1);
-        Aat(i, k) = cadd(cscale(u, c), cmul(cconj(s), w));
-        Aat(i, k + 1) = csub(cscale(w, c), cmul(s, u));
-      }
-      for (int i = tid; i < m; i += nt) {
-        const double2 u = Z[i + (int64_t)k * ld], w = Z[i + (int64_t)(k + 1) * ld];
-        Z[i + (int64_t)k * ld] = cadd(cscale(u, c), cmul(cconj(s), w));
-        Z[i + (int64_t)(k + 1) * ld] = csub(cscale(w, c), cmul(s, u));
+        const double2 un = cadd(cscale(u, c), cmul(cconj(sr), w));
+        Aat(i, k) = un;
+        Aat(i, k + 1) = csub(cscale(w, c), cmul(sr, u));
+        // the next rotation reads A(k+1, k) and A(k+2, k)
+        if (i == k + 1) nx[(k + 1 - l) & 1] = un;
+        if (i == k + 2) ny[(k + 1 - l) & 1] = un;
       }
       __syncthreads();
     }
+    // deferred: rows k, k+1 right of the window, columns k, k+1 above it, and Z
+    for (int j = hi + 1 + tid; j < m; j += nt) {
+      double2 a = Aat(l, j);
+      for (int k = l; k < hi; ++k) {
+        const double c = rot_c[k];
+        const double2 sr = rot_s[k];
+        const double2 b = Aat(k + 1, j);
+        Aat(k, j) = cadd(cscale(a, c), cmul(sr, b));
+        a = csub(cscale(b, c), cmul(cconj(sr), a));
+      }
+      Aat(hi, j) = a;
+    }
+    for (int i = tid; i < l; i += nt) {
+      double2 u = Aat(i, l);
+      for (int k = l; k < hi; ++k) {
+        const double c = rot_c[k];
+        const double2 sr = rot_s[k];
+        const double2 w = Aat(i, k + 1);
+        Aat(i, k) = cadd(cscale(u, c), cmul(cconj(sr), w));
+        u = csub(cscale(w, c), cmul(sr, u));
+      }
+      Aat(i, hi) = u;
+    }
+    for (int i = tid; i < m; i += nt) {
+      double2 u = Z[i + (int64_t)l * ld];
+      for (int k = l; k < hi; ++k) {
+        const double c = rot_c[k];
+        const double2 sr = rot_s[k];
+        const double2 w = Z[i + (int64_t)(k + 1) * ld];
+        Z[i + (int64_t)k * ld] = cadd(cscale(u, c), cmul(cconj(sr), w));
+        u = csub(cscale(w, c), cmul(sr, u));
+      }
+      Z[i + (int64_t)hi * ld] = u;
+    }
+    __syncthreads();
   }
   __syncthreads();
   // ---- select eigenvalues strictly inside the ring

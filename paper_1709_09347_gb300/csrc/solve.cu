@@ -30,7 +30,7 @@ struct cbs_result {
   std::vector<cbs_energy_result> e;
   double ms_solve = 0, ms_moments = 0, ms_extract = 0, ms_total = 0;
   double ms_svd = 0, ms_reduced = 0, ms_vectors = 0;   // parts of ms_extract
-  double prof_ms[2] = {0, 0}, prof_launches[2] = {0, 0}, prof_outputs[2] = {0, 0};
+  double prof_ms[3] = {0, 0, 0}, prof_launches[3] = {0, 0, 0}, prof_outputs[3] = {0, 0, 0};
 };
 
 namespace cbs {
@@ -193,7 +193,7 @@ struct ShiftedSolver {
   std::vector<double> maxrel;
   int sweeps = 0;
   bool fp64_continued = false;
-  double prof_ms[2] = {0, 0}, prof_launches[2] = {0, 0}, prof_outputs[2] = {0, 0};
+  double prof_ms[3] = {0, 0, 0}, prof_launches[3] = {0, 0, 0}, prof_outputs[3] = {0, 0, 0};
   cbs_status collect_profile(cudaStream_t st) {
     double o64 = 0, o32 = 0;
     if (b64.block && b64.profile) CBS_TRY(b64.prof_outputs(st, &o64));
@@ -264,6 +264,9 @@ struct ShiftedSolver {
     double oseed = 0;
     if (o.profile) CBS_TRY(ms.seed.prof_outputs(st, &oseed));
     const double seed_ms = ms.seed.prof_ms, seed_launches = ms.seed.prof_launches;
+    double upd_cols = 0;
+    if (o.profile) CBS_TRY(ms.update_columns(st, &upd_cols));
+    const double upd_ms = ms.upd_ms, upd_launches = ms.upd_launches;
     ms.release();   // keeps X (= Y)
     if (unconv > 0) {
       // plain FP64 BiCG on P(z) D = R, P(z)^dagger D~ = R~ for the columns left, Y += D
@@ -294,6 +297,9 @@ struct ShiftedSolver {
     prof_ms[CBS_C128] += seed_ms;
     prof_launches[CBS_C128] += seed_launches;
     prof_outputs[CBS_C128] += oseed;
+    prof_ms[2] = upd_ms;
+    prof_launches[2] = upd_launches;
+    prof_outputs[2] = upd_cols * (double)H.n;
     return CBS_OK;
   }
 
@@ -520,7 +526,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
       CBS_TRY(S.run_family(H, ne, n_int, L, z1, energies + e0, zs, Es, dV, o, st));
     else
       CBS_TRY(S.run(H, nsys, L, zs, Es, dV, o, st));
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < 3; ++t) {
       res->prof_ms[t] += S.prof_ms[t];
       res->prof_launches[t] += S.prof_launches[t];
       res->prof_outputs[t] += S.prof_outputs[t];
@@ -813,7 +819,10 @@ extern "C" cbs_status cbs_result_timing(const cbs_result *r, double *ms_solve, d
 
 extern "C" cbs_status cbs_result_profile(const cbs_result *r, int dtype, double *ms, double *launches,
                                          double *outputs) {
-  if (!r || (dtype != CBS_C128 && dtype != CBS_C64)) { set_error("bad result or dtype"); return CBS_EINVAL; }
+  if (!r || (dtype != CBS_C128 && dtype != CBS_C64 && dtype != CBS_PROFILE_SHIFT_UPDATE)) {
+    set_error("bad result or dtype");
+    return CBS_EINVAL;
+  }
   if (ms) *ms = r->prof_ms[dtype];
   if (launches) *launches = r->prof_launches[dtype];
   if (outputs) *outputs = r->prof_outputs[dtype];
