@@ -280,6 +280,31 @@ __global__ void k_scale_cols(int n, int ldm, const int *mhat, const double *sig,
 // T = Z^dagger B Z, then eigenvectors of T by back substitution for the selected
 // eigenvalues (those strictly inside the ring), compacted into Yc (m x n_ring) and
 // transformed by Z outside this kernel.
+// Complex Givens rotation [c s; -conj(s) c] with c real that maps (x, y) to (r, 0):
+// c = |x| / rho, s = (x / |x|) conj(y) / rho, rho = sqrt(|x|^2 + |y|^2).  Computed by one
+// thread on the critical path of the QR sweep, so it uses few dependent FP64 operations
+// (one reciprocal square root); the scaled form guards tiny or huge entries.
+__device__ __forceinline__ void givens(double2 x, double2 y, double &c, double2 &s) {
+  const double nx2 = x.x * x.x + x.y * x.y, ny2 = y.x * y.x + y.y * y.y;
+  if (ny2 == 0) { c = 1; s = make_double2(0, 0); return; }
+  if (nx2 == 0) {
+    const double t = rsqrt(ny2);
+    c = 0;
+    s = make_double2(y.x * t, -y.y * t);
+    return;
+  }
+  double p = nx2 * (nx2 + ny2);
+  if (p > 1e-280 && p < 1e280) {
+    const double t = rsqrt(p);                          // 1 / (|x| rho)
+    c = nx2 * t;
+    s = cscale(cmul(x, cconj(y)), t);
+    return;
+  }
+  const double ax = cabsd(x), ay = cabsd(y), rho = hypot(ax, ay);
+  c = ax / rho;
+  s = cscale(cmul(make_double2(x.x / ax, x.y / ax), cconj(y)), 1.0 / rho);
+}
+
 constexpr int kEigThreads = 512;
 constexpr int kMaxEigN = 512;   // largest eigenproblem (launch_eig rejects larger)
 // shift: 0 selects eigenvalues tau inside the ring; otherwise the eigenvalues are mu of a
@@ -297,7 +322,6 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double2 v[512];
   __shared__ double shr[40];
-  __shared__ double2 sh_mu;
   __shared__ int sh_l, sh_hi, sh_act, sh_fail;
   if (m == 0) {
     if (tid == 0) { nring[e] = 0; info[e] = 0; }
@@ -357,12 +381,16 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
   // the window (rows k, k+1 right of hi, columns k, k+1 above l) and the Schur vectors Z are
   // not read by the chase; they receive the sweep's rotations afterwards in one parallel
   // pass, each thread applying them in order to its own column or row (the same operations
-  // per element, in the same order).  The next rotation's inputs pass through a
-  // double-buffered shared slot, so a rotation needs two block barriers.
+  // per element, in the same order).  Every rotation is computed once, by the thread that
+  // owns the two entries defining it, and shared through one slot: two block barriers per
+  // rotation.  (FP64 on this part runs about 1.6 lanes per clock per SM and a warp
+  // instruction costs the same with one active lane as with 32, so redundant per-thread
+  // computation of the rotation is what must be avoided.)
   const double eps = 2.220446049250313e-16;
   __shared__ double rot_c[kMaxEigN];
   __shared__ double2 rot_s[kMaxEigN];
-  __shared__ double2 nx[2], ny[2];
+  __shared__ double sh_c;
+  __shared__ double2 sh_s;
   __shared__ int sh_defl[kEigThreads / 32];
   if (tid == 0) { sh_hi = m - 1; sh_fail = 0; }
   __syncthreads();
@@ -413,11 +441,13 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
             const double2 m1 = cadd(mean, disc), m2 = csub(mean, disc);
             mu = (cabs2(csub(m1, d)) <= cabs2(csub(m2, d))) ? m1 : m2;
           }
-          sh_mu = mu;
           sh_l = l;
           sh_act = 1;
-          nx[0] = csub(Aat(l, l), mu);
-          ny[0] = Aat(l + 1, l);
+          double c0;
+          double2 s0;
+          givens(csub(Aat(l, l), mu), Aat(l + 1, l), c0, s0);
+          sh_c = c0;
+          sh_s = s0;
         }
       }
     }
@@ -427,18 +457,8 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
     if (act == 0) continue;
     const int l = sh_l, hi = sh_hi;
     for (int k = l; k < hi; ++k) {
-      const double2 x = nx[(k - l) & 1], y = ny[(k - l) & 1];
-      const double ax = cabsd(x), ay = cabsd(y);
-      const double rho = hypot(ax, ay);
-      double c;
-      double2 sr;
-      if (rho == 0) { c = 1; sr = make_double2(0, 0); }
-      else if (ax == 0) { c = 0; sr = make_double2(y.x / ay, -y.y / ay); }   // conj(y)/|y|
-      else {
-        c = ax / rho;
-        const double2 phx = make_double2(x.x / ax, x.y / ax);
-        sr = cscale(cmul(phx, cconj(y)), 1.0 / rho);
-      }
+      const double c = sh_c;
+      const double2 sr = sh_s;
       if (tid == 0) { rot_c[k] = c; rot_s[k] = sr; }
       // rows k, k+1 inside the window:  [a; b] <- [c a + s b; -conj(s) a + c b]
       const int j0 = (k == l) ? l : k - 1;
@@ -448,17 +468,32 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
         Aat(k + 1, j) = csub(cscale(b, c), cmul(cconj(sr), a));
       }
       __syncthreads();
-      if (k > l && tid == 0) Aat(k + 1, k - 1) = make_double2(0, 0);
-      // columns k, k+1 inside the window:  [u, w] <- [c u + conj(s) w, -s u + c w]
+      // columns k, k+1 inside the window:  [u, w] <- [c u + conj(s) w, -s u + c w];
+      // thread 0 takes rows k+1 and k+2, whose column-k entries define the next rotation
       const int i1 = min(k + 2, hi);
-      for (int i = l + tid; i <= i1; i += nt) {
-        const double2 u = Aat(i, k), w = Aat(i, k + 1);
-        const double2 un = cadd(cscale(u, c), cmul(cconj(sr), w));
-        Aat(i, k) = un;
-        Aat(i, k + 1) = csub(cscale(w, c), cmul(sr, u));
-        // the next rotation reads A(k+1, k) and A(k+2, k)
-        if (i == k + 1) nx[(k + 1 - l) & 1] = un;
-        if (i == k + 2) ny[(k + 1 - l) & 1] = un;
+      if (tid == 0) {
+        if (k > l) Aat(k + 1, k - 1) = make_double2(0, 0);   // the bulge the rotation removed
+        double2 xn = make_double2(0, 0), yn = make_double2(0, 0);
+        for (int i = k + 1; i <= i1; ++i) {
+          const double2 u = Aat(i, k), w = Aat(i, k + 1);
+          const double2 un = cadd(cscale(u, c), cmul(cconj(sr), w));
+          Aat(i, k) = un;
+          Aat(i, k + 1) = csub(cscale(w, c), cmul(sr, u));
+          if (i == k + 1) xn = un; else yn = un;
+        }
+        if (k + 1 < hi) {
+          double cn;
+          double2 sn;
+          givens(xn, yn, cn, sn);
+          sh_c = cn;
+          sh_s = sn;
+        }
+      } else {
+        for (int i = l + tid - 1; i <= k; i += nt - 1) {
+          const double2 u = Aat(i, k), w = Aat(i, k + 1);
+          Aat(i, k) = cadd(cscale(u, c), cmul(cconj(sr), w));
+          Aat(i, k + 1) = csub(cscale(w, c), cmul(sr, u));
+        }
       }
       __syncthreads();
     }
