@@ -52,6 +52,9 @@ def _peaks():
 
 # GB300 FP64: 1.25 TFLOP/s nominal (152 SMs x 2.07 GHz x 4 FLOP/clk/SM).
 FP64_PEAK_TFLOPS = 1.25
+# FP64 FMA rate measured on this GB300 (independent DFMA chains in every warp of 8 blocks
+# per SM): 1.003 TFLOP/s = 0.5 T lane-instructions per second
+FP64_FMA_MEASURED_TFLOPS = 1.003
 
 
 def _apply_sha():
@@ -68,6 +71,20 @@ def flops_per_output(wl):
     if wl.projectors is not None:
         npj = wl.projectors.n_proj
         f += wl.projectors.nnz / wl.grid.n * (8 * npj + 2)
+    return f
+
+
+def fp64_instr_per_output(wl):
+    """FP64 lane-instructions the complex128 apply issues per complex output: per FD
+    half-width step and component three pair sums and three FMAs (12 per step), 3 for the
+    diagonal term; per covering projector entry 2*n_proj FMAs in the gather and 2*n_proj in
+    the scatter, plus a complex multiply-add (4) for entries of a displaced image."""
+    m = wl.grid.fd_order // 2
+    f = 12 * m + 3
+    if wl.projectors is not None:
+        P = wl.projectors
+        wrapped = float((P.sup_wrap != 0).mean()) if P.nnz else 0.0
+        f += P.nnz / wl.grid.n * (4 * P.n_proj + 4 * wrapped)
     return f
 
 
@@ -361,27 +378,40 @@ def main():
         else:
             fpo = flops_per_output(wl)
             ach = p["outputs"] * fpo / (p["ms"] / 1e3) / 1e12
+            ipo = fp64_instr_per_output(wl)
+            pipe = ipo * p["outputs"] / (p["ms"] / 1e3) / (FP64_FMA_MEASURED_TFLOPS * 1e12 / 2)
             rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
                       frac=ach / FP64_PEAK_TFLOPS, traffic=traffic,
                       peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
-                      flops_per_output=fpo, flops_per_launch=fpo * p["outputs"] / max(p["launches"], 1))
+                      flops_per_output=fpo, flops_per_launch=fpo * p["outputs"] / max(p["launches"], 1),
+                      fp64_instr_per_output=ipo, fp64_pipe_frac_of_measured=pipe,
+                      measured_fp64_fma_tflops=FP64_FMA_MEASURED_TFLOPS)
         return rl
 
     def roofline_shift_update(results):
-        """HBM roofline of the shifted-family update kernel: per (energy, point, column)
-        triple and grid point it reads and writes the scaled direction and the solution,
-        primal and dual (8 x 16 B); the seed residual it also reads is shared by all
-        energies of a point and not counted (a lower bound on the algorithmic bytes)."""
+        """Roofline of the shifted-family update kernel.  Per (energy, point, column) triple
+        and grid point it issues 16 FP64 FMAs (two complex multiply-adds, primal and dual)
+        and moves the scaled direction and the solution in and out, primal and dual
+        (8 x 16 B; the seed residual it also reads is shared by all energies of a point and
+        not counted).  FP64 issue binds first on this part, so the FP64 rate is the roofline
+        and the HBM rate is reported beside it."""
         p = {f: sum(r.profile["shift_update"][f] for r in results) for f in ("ms", "launches", "outputs")}
         if not p["ms"]:
             return None
-        bpo = 8 * 16
-        ach = p["outputs"] * bpo / (p["ms"] / 1e3) / 1e9
+        bpo, ipo = 8 * 16, 16
+        sec = p["ms"] / 1e3
+        ach = p["outputs"] * 2 * ipo / sec / 1e12
+        gbs = p["outputs"] * bpo / sec / 1e9
         return {"kernel": "k_ms_update: shifted-family direction and solution update",
                 "outputs": p["outputs"], "launches": p["launches"],
-                "avg_launch_ms": p["ms"] / max(p["launches"], 1), "bound": "hbm", "achieved": ach,
-                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-                "peak_source": hbm_src, "bytes_per_output": bpo,
+                "avg_launch_ms": p["ms"] / max(p["launches"], 1), "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
+                "fp64_instr_per_output": ipo,
+                "fp64_pipe_frac_of_measured": ach / FP64_FMA_MEASURED_TFLOPS,
+                "measured_fp64_fma_tflops": FP64_FMA_MEASURED_TFLOPS,
+                "hbm_achieved_GB_s": gbs, "hbm_peak_GB_s": hbm, "hbm_frac": gbs / hbm,
+                "hbm_peak_source": hbm_src, "bytes_per_output": bpo,
                 "bytes_per_launch": bpo * p["outputs"] / max(p["launches"], 1)}
 
     def summary(results):
@@ -436,7 +466,7 @@ def main():
     # solve, results (eigenvalues, k, residuals, eigenvectors) back to the host
     def e2e_step():
         Hh = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
-        cbs.set_apply_shape(Hh, torch.complex128, tune["c128"]["py"])
+        cbs.set_apply_shape(Hh, torch.complex128, tune["c128"]["py"], tune["c128"]["pz"])
         r = cbs.solve(Hh, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
                       cbs.options(precision="fp64", tol=wl.tol, delta=wl.delta,
                                   multi_shift=1 if shift else 0))

@@ -173,25 +173,27 @@ cbs_status cbs_apply_noalloc(const cbs_hamiltonian *h, int n_sys, const double *
 
 /* Autotuner for the operator apply (not in the paper, whose code has fixed launch shapes).
  * Times every admissible launch shape of the stencil kernel on n_sys systems of L columns
- * of type dtype (x-lines of the grid per thread block: 1, 2, 4, ... up to 256 threads; for
- * complex64 with even L and at most 4 projectors, also one versus two columns per
- * thread), with CUDA events on `stream`, a few applies each, and stores the fastest in h:
+ * of type dtype (a thread block covers py x-lines of pz grid rows, py, pz powers of two, up
+ * to 256 threads; for complex64 with even L and at most 4 projectors, also one versus two
+ * columns per thread), with CUDA events on `stream`, a few applies each, and stores the
+ * fastest in h:
  * every later apply of that precision through h (cbs_apply*, cbs_solve*, cbs_objective)
  * uses it.  Allocates and frees its own buffers (about 2 n_sys N L elements) and
- * synchronises `stream`.  Outputs (may be NULL): best_py (x-lines per block), best_x2
- * (1 two columns per thread, -1 one, 0 not applicable), best_ms (one apply, milliseconds).
+ * synchronises `stream`.  Outputs (may be NULL): best_py, best_pz (x-lines and rows per
+ * block), best_x2 (1 two columns per thread, -1 one, 0 not applicable), best_ms (one
+ * apply, milliseconds).
  * Must not run concurrently with other work that uses h.  Every shape computes the same
  * arithmetic per output; the one- and two-column complex64 kernels may differ in the last
  * bit. */
 cbs_status cbs_autotune_apply(cbs_hamiltonian *h, int n_sys, int L, int dtype, void *stream,
-                              int *best_py, int *best_x2, float *best_ms);
+                              int *best_py, int *best_pz, int *best_x2, float *best_ms);
 
 /* Sets the launch shape that cbs_autotune_apply would store (e.g. one tuned on another
- * handle of the same cell): py x-lines per block (0 = default), x2 as best_x2 above
- * (complex64 only; ignored for complex128).  A shape that does not fit a launch (py times
- * the threads of one x-line above 256) is ignored at launch time.  Must not run
- * concurrently with other work that uses h. */
-cbs_status cbs_set_apply_shape(cbs_hamiltonian *h, int dtype, int py, int x2);
+ * handle of the same cell): py x-lines of pz rows per block (0 = default), x2 as best_x2
+ * above (complex64 only; ignored for complex128).  A shape that does not fit a launch (py
+ * times pz times the threads of one x-line above 256) is ignored at launch time.  Must not
+ * run concurrently with other work that uses h. */
+cbs_status cbs_set_apply_shape(cbs_hamiltonian *h, int dtype, int py, int pz, int x2);
 
 /* Shifted solves of §3.2 for a batch of n_sys points: BiCG on P(z_s) Y[s] = B and, as
  * its dual, P(z_s)^dagger Yd[s] = B (= P(1/conj z_s) Yd[s] = B).

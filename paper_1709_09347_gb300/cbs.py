@@ -111,8 +111,8 @@ def load():
     lib.cbs_apply_ws.argtypes = [V, I, V, V, I, V, V, I, V, ct.c_size_t, V]
     lib.cbs_apply_noalloc.argtypes = [V, I, P(D), P(D), I, V, V, I, V]
     lib.cbs_objective.argtypes = [V, D, P(Contour), I, I, V, P(Options), P(D), P(D), P(D)]
-    lib.cbs_autotune_apply.argtypes = [V, I, I, I, V, P(I), P(I), P(ct.c_float)]
-    lib.cbs_set_apply_shape.argtypes = [V, I, I, I]
+    lib.cbs_autotune_apply.argtypes = [V, I, I, I, V, P(I), P(I), P(I), P(ct.c_float)]
+    lib.cbs_set_apply_shape.argtypes = [V, I, I, I, I]
     lib.cbs_kernel_launches.argtypes = []
     lib.cbs_kernel_launches.restype = ct.c_uint64
     _lib = lib
@@ -303,17 +303,17 @@ def autotune_apply(H: Hamiltonian, n_sys: int, L: int, dtype) -> dict:
     fastest in H (cbs_autotune_apply); dtype is torch.complex128 or torch.complex64."""
     import torch
     code = CBS_C64 if dtype == torch.complex64 else CBS_C128
-    py, x2, ms = ct.c_int(0), ct.c_int(0), ct.c_float(0)
+    py, pz, x2, ms = ct.c_int(0), ct.c_int(0), ct.c_int(0), ct.c_float(0)
     _check(load().cbs_autotune_apply(H.handle, int(n_sys), int(L), code, _stream_ptr(torch),
-                                     ct.byref(py), ct.byref(x2), ct.byref(ms)))
-    return {"py": py.value, "x2": x2.value, "ms": ms.value}
+                                     ct.byref(py), ct.byref(pz), ct.byref(x2), ct.byref(ms)))
+    return {"py": py.value, "pz": pz.value, "x2": x2.value, "ms": ms.value}
 
 
-def set_apply_shape(H: Hamiltonian, dtype, py: int, x2: int = 0) -> None:
+def set_apply_shape(H: Hamiltonian, dtype, py: int, pz: int = 1, x2: int = 0) -> None:
     """Store a launch shape (as returned by autotune_apply) in H (cbs_set_apply_shape)."""
     import torch
     code = CBS_C64 if dtype == torch.complex64 else CBS_C128
-    _check(load().cbs_set_apply_shape(H.handle, code, int(py), int(x2)))
+    _check(load().cbs_set_apply_shape(H.handle, code, int(py), int(pz), int(x2)))
 
 
 def kernel_launches() -> int:

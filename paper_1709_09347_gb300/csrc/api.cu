@@ -122,7 +122,7 @@ extern "C" cbs_status cbs_apply_ws(const cbs_hamiltonian *h, int n_sys, const do
 // is timed with CUDA events on `stream` over a few applies of n_sys systems, and the
 // fastest is stored in the handle, where every later apply of that precision uses it.
 extern "C" cbs_status cbs_autotune_apply(cbs_hamiltonian *h, int n_sys, int L, int dtype,
-                                         void *stream, int *best_py, int *best_x2,
+                                         void *stream, int *best_py, int *best_pz, int *best_x2,
                                          float *best_ms) {
   if (!h || n_sys < 1 || L < 1 || L > 512) {
     set_error("cbs_autotune_apply: bad argument (need n_sys >= 1, 1 <= L <= 512)");
@@ -151,8 +151,8 @@ extern "C" cbs_status cbs_autotune_apply(cbs_hamiltonian *h, int n_sys, int L, i
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cbs_status s = CBS_OK;
-  const int keep_py = H.tune_py[ti], keep_x2 = H.tune_x2;
-  int bp = 0, bx = 0;
+  const int keep_py = H.tune_py[ti], keep_pz = H.tune_pz[ti], keep_x2 = H.tune_x2;
+  int bp = 0, bz = 0, bx = 0;
   float bms = 0.f;
   auto run = [&]() -> cbs_status {
     if (dtype == CBS_C128)
@@ -173,8 +173,10 @@ extern "C" cbs_status cbs_autotune_apply(cbs_hamiltonian *h, int n_sys, int L, i
     for (int vi = 0; vi < (x2_ok ? 2 : 1) && s == CBS_OK; ++vi) {
       const int x2 = x2_ok ? variants[vi] : 0;
       const int per_line = (x2_ok && x2 > 0) ? L / 2 : L;
-      for (int py = 1; py * per_line <= 256 && py <= 32 && s == CBS_OK; py *= 2) {
+      for (int py = 1; py * per_line <= 256 && py <= 32 && s == CBS_OK; py *= 2)
+      for (int pz = 1; py * pz * per_line <= 256 && pz <= 16 && s == CBS_OK; pz *= 2) {
         H.tune_py[ti] = py;
+        H.tune_pz[ti] = pz;
         H.tune_x2 = x2;
         for (int w = 0; w < 2 && s == CBS_OK; ++w) s = run();
         if (s != CBS_OK) break;
@@ -187,7 +189,7 @@ extern "C" cbs_status cbs_autotune_apply(cbs_hamiltonian *h, int n_sys, int L, i
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e != cudaSuccess) { s = cuda_fail(e, "cbs_autotune_apply timing"); break; }
         ms /= reps;
-        if (bp == 0 || ms < bms) { bp = py; bx = x2; bms = ms; }
+        if (bp == 0 || ms < bms) { bp = py; bz = pz; bx = x2; bms = ms; }
       }
     }
   } while (0);
@@ -197,24 +199,29 @@ extern "C" cbs_status cbs_autotune_apply(cbs_hamiltonian *h, int n_sys, int L, i
   cudaFree(buf);
   if (s != CBS_OK || bp == 0) {
     H.tune_py[ti] = keep_py;
+    H.tune_pz[ti] = keep_pz;
     H.tune_x2 = keep_x2;
     return s != CBS_OK ? s : CBS_EINVAL;
   }
   H.tune_py[ti] = bp;
+  H.tune_pz[ti] = bz;
   H.tune_x2 = ti == 1 ? bx : keep_x2;
   if (best_py) *best_py = bp;
+  if (best_pz) *best_pz = bz;
   if (best_x2) *best_x2 = bx;
   if (best_ms) *best_ms = bms;
   return CBS_OK;
 }
 
-extern "C" cbs_status cbs_set_apply_shape(cbs_hamiltonian *h, int dtype, int py, int x2) {
-  if (!h || (dtype != CBS_C128 && dtype != CBS_C64) || py < 0 || py > 256 || x2 < -1 || x2 > 1) {
+extern "C" cbs_status cbs_set_apply_shape(cbs_hamiltonian *h, int dtype, int py, int pz, int x2) {
+  if (!h || (dtype != CBS_C128 && dtype != CBS_C64) || py < 0 || py > 256 || pz < 0 || pz > 256 ||
+      x2 < -1 || x2 > 1) {
     set_error("cbs_set_apply_shape: bad argument");
     return CBS_EINVAL;
   }
   HamView &H = h->v;
   H.tune_py[dtype == CBS_C64 ? 1 : 0] = py;
+  H.tune_pz[dtype == CBS_C64 ? 1 : 0] = pz;
   if (dtype == CBS_C64) H.tune_x2 = x2;
   return CBS_OK;
 }

@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typena
   if (sys_active && !sys_active[s]) return;
   const int c = threadIdx.x;
   const int ix = blockIdx.x * blockDim.y + threadIdx.y;
-  const int iy = blockIdx.y;
-  if (ix >= H.nx) return;
+  const int iy = blockIdx.y * blockDim.z + threadIdx.z;   // a block covers blockDim.z rows
+  if (ix >= H.nx || iy >= H.ny) return;
   const int nx = H.nx, ny = H.ny, nz = H.nz;
   const int nxy = nx * ny;
   double2 wd = twist[PER_COL ? (int64_t)s * L + c : s];
@@ -348,8 +348,8 @@ __global__ void __launch_bounds__(256, 3) k_apply_c64x2(HamView H, int L, const 
   const int t = threadIdx.x;                 // column pair
   const int L2 = L >> 1;
   const int ix = blockIdx.x * blockDim.y + threadIdx.y;
-  const int iy = blockIdx.y;
-  if (ix >= H.nx) return;
+  const int iy = blockIdx.y * blockDim.z + threadIdx.z;   // a block covers blockDim.z rows
+  if (ix >= H.nx || iy >= H.ny) return;
   const int nx = H.nx, ny = H.ny, nz = H.nz, nxy = nx * ny;
   const double2 wd0 = twist[PER_COL ? (int64_t)s * L + 2 * t : s];
   const double2 wd1 = twist[PER_COL ? (int64_t)s * L + 2 * t + 1 : s];
@@ -468,11 +468,14 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
   // complex64 with an even number of columns and at most 4 projectors: two columns per thread
   if (ti == 1 && L % 2 == 0 && L <= 512 && H.np4 == 4 && H.tune_x2 >= 0) {
     const int L2 = L / 2;
-    int py = 256 / L2;
-    if (H.tune_py[1] > 0 && H.tune_py[1] * L2 <= 256) py = H.tune_py[1];
+    int py = 256 / L2, pz = 1;
+    if (H.tune_py[1] > 0 && H.tune_pz[1] > 0 && H.tune_py[1] * H.tune_pz[1] * L2 <= 256) {
+      py = H.tune_py[1];
+      pz = H.tune_pz[1];
+    }
     if (py < 1) py = 1;
-    dim3 blk((unsigned)L2, (unsigned)py, 1);
-    dim3 grd((unsigned)ceil_div(H.nx, py), (unsigned)H.ny, (unsigned)n_sys);
+    dim3 blk((unsigned)L2, (unsigned)py, (unsigned)pz);
+    dim3 grd((unsigned)ceil_div(H.nx, py), (unsigned)ceil_div(H.ny, pz), (unsigned)n_sys);
     const float4 *X4 = reinterpret_cast<const float4 *>(X);
     float4 *Y4 = reinterpret_cast<float4 *>(Y);
     const float4 *D4 = H.n_atoms ? reinterpret_cast<const float4 *>(D) : nullptr;
@@ -496,12 +499,15 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
     return CBS_OK;
   }
   dim3 blk = col_block(L);
-  if (H.tune_py[ti] > 0 && H.tune_py[ti] * L <= 256) blk.y = (unsigned)H.tune_py[ti];
-  if (blk.x * blk.y > 256) {
+  if (H.tune_py[ti] > 0 && H.tune_pz[ti] > 0 && H.tune_py[ti] * H.tune_pz[ti] * L <= 256) {
+    blk.y = (unsigned)H.tune_py[ti];
+    blk.z = (unsigned)H.tune_pz[ti];
+  }
+  if (blk.x * blk.y * blk.z > 256) {
     set_error("apply: at most 256 columns per system (512 in complex64 with even L)");
     return CBS_EINVAL;
   }
-  dim3 grd((unsigned)ceil_div(H.nx, blk.y), (unsigned)H.ny, (unsigned)n_sys);
+  dim3 grd((unsigned)ceil_div(H.nx, blk.y), (unsigned)ceil_div(H.ny, blk.z), (unsigned)n_sys);
 #define ZM(MH)                                                                                  \
   do {                                                                                          \
     if (per_col) k_apply_zm<R, true, MH><<<grd, blk, 0, st>>>(H, L, X, Y, twist, E, Dp, sys_active); \

@@ -101,9 +101,10 @@ struct HamView {
   const int2 *pt_aw;        // [nnz] (atom, wrap) of each covering entry, point order
   const float4 *pt_p32;     // [nnz] projector values of the entry, zero-padded to 4 (n_proj <= 4)
   // stencil launch shape chosen by cbs_autotune_apply, per precision ([0] complex128,
-  // [1] complex64): x-lines per block (0 = default 256 / threads per line) and, for
-  // complex64, whether the two-columns-per-thread kernel is used (1 = yes, 0 = default, -1 = no)
-  int tune_py[2];
+  // [1] complex64): a block covers tune_py x-lines of tune_pz rows (0 = default: 256 /
+  // threads per line x-lines of one row) and, for complex64, whether the
+  // two-columns-per-thread kernel is used (1 = yes, 0 = default, -1 = no)
+  int tune_py[2], tune_pz[2];
   int tune_x2;
 };
 

@@ -64,7 +64,8 @@ def test_autotuned_apply(name, L):
     H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
     t128 = cbs.autotune_apply(H, 8, L, torch.complex128)
     t64 = cbs.autotune_apply(H, 8, L, torch.complex64)
-    assert t128["py"] >= 1 and t128["py"] * L <= 256 and t128["ms"] > 0
+    assert t128["py"] >= 1 and t128["pz"] >= 1 and t128["py"] * t128["pz"] * L <= 256
+    assert t128["ms"] > 0
     assert t64["x2"] in ((1, -1) if L % 2 == 0 else (0,))
     assert _run(wl, ZS, ES, L, "c128", H) < 1e-13
     assert _run(wl, ZS, ES, L, "c64", H) < 3e-6

@@ -250,3 +250,33 @@ def test_solve_multishift_c2_vs_oracle_golden():
         rr = ss.residuals(op, E, r["lam"], r["vectors"], op.frobenius(E))
         assert np.all(rr <= 1e-8)
         assert r["max_solve_residual"] <= 1e-9
+
+
+def test_solve_multishift_single_energy_and_rr():
+    """Shifted family with one energy (the seed alone, shift 0) and with the Rayleigh-Ritz
+    extraction: eigenpairs as the oracle's per-energy runs of the same extraction."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3,
+                             L=12, M=8, n_int=32, energies=(0.2, -0.3))
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    one = cbs.solve(H, wl.energies[:1], wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=1e-12, multi_shift=1)).energies[0]
+    _compare(one, ss.ss_hankel(op, float(wl.energies[0]), wl.lambda_min, wl.n_int, wl.V, wl.M,
+                               tol=1e-12), 1e-10)
+    rr = cbs.solve(H, wl.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                   cbs.options(tol=1e-12, multi_shift=1, extraction="rr"))
+    for e, E in enumerate(wl.energies):
+        _compare(rr.energies[e], ss.ss_rayleigh_ritz(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M,
+                                                     tol=1e-12), 1e-10)
+
+
+def test_multishift_needs_fp64():
+    """multi_shift is defined for the FP64 form only; the mixed form rejects it."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = small_cases()[0]
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    with pytest.raises(cbs.CbsError):
+        cbs.solve(H, [0.1], 0.5, 8, wl.L, 2, wl.V, cbs.options(precision="fp32_refine", multi_shift=1))
