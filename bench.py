@@ -38,7 +38,10 @@ UNIT = "energies/s"
 
 # DRAM traffic of the FP64 stencil+projector apply per complex output, from one ncu
 # capture (profiles/apply_fp64_c2.md), valid while csrc/apply.cu hashes to APPLY_SHA.
-APPLY_TRAFFIC = {"sha": None, "c128_bytes_per_output": None, "c64_bytes_per_output": None}
+# DRAM bytes per output of the apply pair (stencil + projector gather) from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, 64 systems of the 32x32x16 cell, L = 32,
+# tuned shape); valid while apply.cu has this hash
+APPLY_TRAFFIC = {"sha": "a48a73a6d3be70a8", "c128_bytes_per_output": 45.467, "c64_bytes_per_output": None}
 
 
 def _peaks():
