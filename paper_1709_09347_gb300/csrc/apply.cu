@@ -18,6 +18,20 @@
 
 namespace cbs {
 
+// A system's twist w and its inverse in the working precision.  In complex64 the inverse is
+// formed in FP32 from the rounded twist: a complex double division costs ~20 FP64
+// instructions per thread, which on this part's narrow FP64 pipe was a visible share of a
+// complex64 launch.
+__device__ __forceinline__ void twist_pair(double2 wd, double2 &w, double2 &wi) {
+  w = wd;
+  wi = cdiv(make_double2(1.0, 0.0), wd);
+}
+__device__ __forceinline__ void twist_pair(double2 wd, float2 &w, float2 &wi) {
+  w = make_float2((float)wd.x, (float)wd.y);
+  const float r = 1.0f / (w.x * w.x + w.y * w.y);
+  wi = make_float2(w.x * r, -w.y * r);
+}
+
 __device__ __forceinline__ float4 c2mul(float2 w0, float2 w1, float4 v) {
   const float2 a = cmul(w0, make_float2(v.x, v.y)), b = cmul(w1, make_float2(v.z, v.w));
   return make_float4(a.x, a.y, b.x, b.y);
@@ -45,9 +59,8 @@ __global__ void k_proj_gather(HamView H, int L, const typename CT<R>::T *__restr
   const int c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
   if (sys_active && !sys_active[s]) return;
   const int np = H.n_proj;
-  double2 wd = twist[PER_COL ? (int64_t)s * L + c : s];
-  double2 wid = cdiv(make_double2(1.0, 0.0), wd);
-  C w = from_d<R>(wd), wi = from_d<R>(wid);
+  C w, wi;
+  twist_pair(twist[PER_COL ? (int64_t)s * L + c : s], w, wi);
   // one accumulator set per image shift m = 0, +1, -1: the twist w^{-m} is applied once
   // per column at the end instead of once per support entry
   C acc[NPM], accp[NPM], accm[NPM];
@@ -151,9 +164,9 @@ __global__ void k_proj_gather_c64x2(HamView H, int L, const float4 *__restrict__
   if (sys_active && !sys_active[s]) return;
   const double2 wd0 = twist[PER_COL ? (int64_t)s * L + 2 * t : s];
   const double2 wd1 = twist[PER_COL ? (int64_t)s * L + 2 * t + 1 : s];
-  const float2 w0 = from_d<float>(wd0), w1 = from_d<float>(wd1);
-  const float2 wi0 = from_d<float>(cdiv(make_double2(1.0, 0.0), wd0));
-  const float2 wi1 = from_d<float>(cdiv(make_double2(1.0, 0.0), wd1));
+  float2 w0, w1, wi0, wi1;
+  twist_pair(wd0, w0, wi0);
+  twist_pair(wd1, w1, wi1);
   float4 acc[4];
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) acc[mu] = make_float4(0, 0, 0, 0);
@@ -248,9 +261,8 @@ __global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typena
   if (ix >= H.nx || iy >= H.ny) return;
   const int nx = H.nx, ny = H.ny, nz = H.nz;
   const int nxy = nx * ny;
-  double2 wd = twist[PER_COL ? (int64_t)s * L + c : s];
-  double2 wid = cdiv(make_double2(1.0, 0.0), wd);
-  const C w = from_d<R>(wd), wi = from_d<R>(wid);
+  C w, wi;
+  twist_pair(twist[PER_COL ? (int64_t)s * L + c : s], w, wi);
   const R ed = (R)(E[s] - H.diag_kin);
   R nwx[MH + 1], nwy[MH + 1], nwz[MH + 1];
   int ox_p[MH + 1], ox_m[MH + 1], oy_p[MH + 1], oy_m[MH + 1];
@@ -353,9 +365,9 @@ __global__ void __launch_bounds__(256, 3) k_apply_c64x2(HamView H, int L, const 
   const int nx = H.nx, ny = H.ny, nz = H.nz, nxy = nx * ny;
   const double2 wd0 = twist[PER_COL ? (int64_t)s * L + 2 * t : s];
   const double2 wd1 = twist[PER_COL ? (int64_t)s * L + 2 * t + 1 : s];
-  const double2 wid0 = cdiv(make_double2(1.0, 0.0), wd0), wid1 = cdiv(make_double2(1.0, 0.0), wd1);
-  const float2 w0 = from_d<float>(wd0), w1 = from_d<float>(wd1);
-  const float2 wi0 = from_d<float>(wid0), wi1 = from_d<float>(wid1);
+  float2 w0, w1, wi0, wi1;
+  twist_pair(wd0, w0, wi0);
+  twist_pair(wd1, w1, wi1);
   const float e = (float)E[s];
   const float dk = H.diag_kin32;
   // neighbour offsets in float4 units (x and y periodic); recomputed, not kept in registers
