@@ -280,3 +280,22 @@ def test_multishift_needs_fp64():
     H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
     with pytest.raises(cbs.CbsError):
         cbs.solve(H, [0.1], 0.5, 8, wl.L, 2, wl.V, cbs.options(precision="fp32_refine", multi_shift=1))
+
+
+def test_scan_batches_and_branches():
+    """An energy scan through scan.scan (batches of 2, the last batch one energy): every
+    energy's pairs as the oracle's, and scan.connect places each pair in exactly one branch."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs, scan
+    energies = (0.1, 0.15, 0.2, 0.25, 0.3)
+    wl = synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3,
+                             L=12, M=8, n_int=32, energies=energies)
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    res = scan.scan(H, wl.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=1e-12, multi_shift=1), batch=2)
+    assert len(res) == len(energies)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    for e, E in enumerate(wl.energies):
+        _compare(res[e], ss.ss_hankel(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12), 1e-10)
+    branches = scan.connect([r["lam"] for r in res], max_jump=1.0)
+    assert sum(len(b.lam) for b in branches) == sum(len(r["lam"]) for r in res)
