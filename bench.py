@@ -41,7 +41,7 @@ UNIT = "energies/s"
 # DRAM bytes per output of the apply pair (stencil + projector gather) from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, 64 systems of the 32x32x16 cell, L = 32,
 # tuned shape); valid while apply.cu has this hash
-APPLY_TRAFFIC = {"sha": "a48a73a6d3be70a8", "c128_bytes_per_output": 45.467, "c64_bytes_per_output": None}
+APPLY_TRAFFIC = {"sha": "e1a5bc6eb446a0ce", "c128_bytes_per_output": 45.437, "c64_bytes_per_output": None}
 
 
 def _peaks():
