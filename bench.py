@@ -2,21 +2,27 @@
 """Benchmark: CBS energies per second at eigenpair residual <= 1e-8, on GB300.
 
 One step = the whole method (contour, batched shifted BiCG solves with their duals,
-moments, Hankel SVD + reduced eigenproblem, residual filter, k) for every energy of the
-workload, through libcbs's C ABI.  Default workload: the 32x32x16 molecular-crystal
-cell (8th-order FD, 40 atoms with 4 projectors each, 16 energies in [-0.5, 0.5] Ha,
-N_int = 32 per circle, L = 32, M = 8) in plain FP64 — the configuration the metric is
-quoted on.  The headline is the FP64 form with one BiCG Krylov sequence per quadrature
-point and column shared by all energies of the step (shifted BiCG, P(z, E) = P(z, E0) +
-(E - E0) I; columns that miss the tolerance on the true residual are finished by plain
-BiCG).  Beside it, on the same workload: the paper's scheme of one FP64 BiCG per (energy,
-quadrature point) ("fp64_per_energy") and complex64 BiCG with FP64 reliable updates
-("fp32_refine").
+moments, Hankel SVD + reduced eigenproblem, residual filter, k) for the energies of the
+step, through libcbs's C ABI.  Default workload: the 64x64x24 precision cell (8th-order
+FD, 120 atoms with 4 projectors each, lambda_min = 0.3, N_int = 64 per circle, L = 32,
+M = 8, BiCG tolerance 1e-10), on four of its 32 energies in [-0.5, 0.5] Ha, one from each
+quarter of the range (indices 3, 11, 19, 27: the BiCG iteration count grows about
+sixty-fold from the bottom of the range to the top, so the step samples all of it).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl reference]
+Forms, all on the same step at the same eigenpair residual bar (rho <= 1e-8):
+  mixed  (headline)  one complex64 BiCG Krylov sequence per quadrature point and column
+                     shared by every energy of the step (shifted BiCG, P(z, E) =
+                     P(z, E0) + (E - E0) I), then per-energy refinement with complex64 BiCG
+                     and FP64 reliable updates to the FP64 tolerance;
+  fp64               the same shifted family in FP64, columns missing the tolerance on the
+                     true residual finished by FP64 BiCG;
+  fp64_per_energy    (--per-energy) one FP64 BiCG per (energy, quadrature point), the
+                     paper's scheme.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3] [--impl reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own copy of the
-energy list (independent problems, no collective on the data path): weak scaling.
+step (independent problems, no collective on the data path): weak scaling.
 """
 from __future__ import annotations
 
@@ -36,12 +42,28 @@ sys.path.insert(0, ROOT)
 METRIC = "CBS energies/sec at residual<=1e-8 (FP32+refine vs FP64); SpMM HBM GB/s"
 UNIT = "energies/s"
 
-# DRAM traffic of the FP64 stencil+projector apply per complex output, from one ncu
-# capture (profiles/apply_fp64_c2.md), valid while csrc/apply.cu hashes to APPLY_SHA.
-# DRAM bytes per output of the apply pair (stencil + projector gather) from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, 64 systems of the 32x32x16 cell, L = 32,
-# tuned shape); valid while apply.cu has this hash
-APPLY_TRAFFIC = {"sha": "e1a5bc6eb446a0ce", "c128_bytes_per_output": 45.437, "c64_bytes_per_output": None}
+# energies of one step per workload (indices into the workload's energy list); workloads
+# not listed take all of their energies
+STEP_ENERGIES = {"c3": (3, 11, 19, 27)}
+
+# DRAM bytes per unit of the kernels reported as rooflines, each from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum divided by the units of the captured
+# launch), valid while the kernel's source file hashes to `sha`
+KERNEL_TRAFFIC = {
+    "c128_apply": {"file": "apply.cu", "sha": None, "bytes_per_unit": None},
+    "c64_apply": {"file": "apply.cu", "sha": None, "bytes_per_unit": None},
+    "c64_shift_update": {"file": "bicg.cu", "sha": None, "bytes_per_unit": None},
+}
+
+FORMS = {
+    "mixed": {"precision": "fp32_refine", "multi_shift": 1,
+              "dtype": "c64 shifted-family BiCG + c64/f64 reliable-update refinement"},
+    "fp64": {"precision": "fp64", "multi_shift": 1, "dtype": "f64"},
+    "fp64_per_energy": {"precision": "fp64", "multi_shift": 0, "dtype": "f64"},
+}
+
+# GB300 FP64: 1.25 TFLOP/s nominal (152 SMs x 2.07 GHz x 4 FLOP/clk/SM).
+FP64_PEAK_TFLOPS = 1.25
 
 
 def _peaks():
@@ -53,52 +75,38 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# GB300 FP64: 1.25 TFLOP/s nominal (152 SMs x 2.07 GHz x 4 FLOP/clk/SM).
-FP64_PEAK_TFLOPS = 1.25
-# FP64 FMA rate measured on this GB300 (independent DFMA chains in every warp of 8 blocks
-# per SM): 1.003 TFLOP/s = 0.5 T lane-instructions per second
-FP64_FMA_MEASURED_TFLOPS = 1.003
-
-
-def _apply_sha():
-    with open(os.path.join(ROOT, "paper_1709_09347_gb300", "csrc", "apply.cu"), "rb") as f:
+def _sha(fname):
+    with open(os.path.join(ROOT, "paper_1709_09347_gb300", "csrc", fname), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def flops_per_output(wl):
-    """Algorithmic real flops per complex output of the operator apply: 2 (diagonal) +
-    18 per FD half-width step (x, y, z pairs) + 4 (E x - acc) + per covering projector
-    entry 4*n_proj (gather) + 4*n_proj + 2 (scatter)."""
-    m = wl.grid.fd_order // 2
-    f = 2 + 18 * m + 4
-    if wl.projectors is not None:
-        npj = wl.projectors.n_proj
-        f += wl.projectors.nnz / wl.grid.n * (8 * npj + 2)
-    return f
+def _traffic(key, units_per_launch):
+    t = KERNEL_TRAFFIC[key]
+    if t["sha"] and t["bytes_per_unit"] and _sha(t["file"]) == t["sha"]:
+        return t["bytes_per_unit"] * units_per_launch
+    return None
 
 
-def fp64_instr_per_output(wl):
-    """FP64 lane-instructions the complex128 apply issues per complex output: per FD
-    half-width step and component three pair sums and three FMAs (12 per step), 3 for the
-    diagonal term; per covering projector entry 2*n_proj FMAs in the gather and 2*n_proj in
-    the scatter, plus a complex multiply-add (4) for entries of a displaced image."""
-    m = wl.grid.fd_order // 2
-    f = 12 * m + 3
-    if wl.projectors is not None:
-        P = wl.projectors
-        wrapped = float((P.sup_wrap != 0).mean()) if P.nnz else 0.0
-        f += P.nnz / wl.grid.n * (4 * P.n_proj + 4 * wrapped)
-    return f
-
-
-def bytes_per_output(wl, s):
-    """Algorithmic bytes per complex output: read X and write Y once (2 s) plus the local
-    potential (s/2 per point) and the projector table (values + index) amortised over L."""
+def apply_bytes_per_output(wl, s):
+    """Algorithmic bytes per complex output of the operator apply: read X and write Y once
+    (2 s) plus the local potential (s/2 per point) and the projector table (values + index)
+    amortised over the L columns."""
     b = 2 * s + (s / 2) / wl.L
     if wl.projectors is not None:
         npj = wl.projectors.n_proj
         b += wl.projectors.nnz / wl.grid.n * (npj * s / 2 + 8) / wl.L
     return b
+
+
+def apply_flops_per_output(wl):
+    """Algorithmic real flops per complex output of the operator apply: 2 (diagonal) + 18
+    per FD half-width step (x, y, z pairs) + 4 (E x - acc) + per covering projector entry
+    4*n_proj (gather) + 4*n_proj + 2 (scatter)."""
+    m = wl.grid.fd_order // 2
+    f = 2 + 18 * m + 4
+    if wl.projectors is not None:
+        f += wl.projectors.nnz / wl.grid.n * (8 * wl.projectors.n_proj + 2)
+    return f
 
 
 class ClockSampler:
@@ -165,66 +173,111 @@ def _dist():
     return world, rank, local
 
 
-def cpu_baseline_sample(workload: str, n_points: int, energy_index: int) -> dict:
-    """Time the oracle (as it stands) on a bounded sample: n_points of the n_int
-    quadrature-point BiCG solves of one energy, single-threaded.  Runs in a child process
-    with one BLAS/OpenMP thread so that `cores` is exact."""
-    code = f"""
-import json, os, sys, time
-sys.path.insert(0, {ROOT!r})
-from paper_1709_09347_gb300 import synth
-from oracle.operator import CellOperator
-from oracle.contour import ring_contour
-from oracle.bicg import bicg
-wl = synth.workload({workload!r})
-op = CellOperator(wl.grid, wl.vloc, wl.projectors)
-E = float(wl.energies[{energy_index}])
-z1 = ring_contour(wl.lambda_min, wl.n_int)[0]
-t = time.time()
-iters = []
-for j in range({n_points}):
-    z = z1[j * (wl.n_int // {n_points})]
-    X, Xt, it, info = bicg(lambda X: op.apply_P(z, E, X), lambda X: op.apply_P_adjoint(z, E, X),
-                           wl.V, wl.V, tol=wl.tol)
-    iters.append(int(it.max()))
-dt = time.time() - t
-print(json.dumps(dict(seconds=dt, iters=iters, n_int=wl.n_int)))
-"""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    per_energy = r["seconds"] * r["n_int"] / n_points
-    return {"value": 1.0 / per_energy, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{workload}: {n_points} of {r['n_int']} quadrature-point BiCG solves "
-                       f"(primal+dual, all L columns) at energy index {energy_index}, "
-                       f"{r['seconds']:.1f} s, iterations {r['iters']}; scaled by n_int/{n_points} "
-                       f"to one energy (extraction not included)"),
-            "seconds": r["seconds"]}
+def step_energy_indices(wl, spec):
+    if spec:
+        return [int(a) for a in spec.split(",")]
+    return list(STEP_ENERGIES.get(wl.name, range(len(wl.energies))))
+
+
+# ---------------------------------------------------------------------- CPU oracle timing
+CPU_SAMPLE = {
+    # workload: (energy index with a stored oracle run, BiCG iterations to time per point)
+    "c3": (0, "tests/golden/c3_oracle_e00.npz", 12),
+    "c2": (3, "tests/golden/c2_oracle.npz", 12),
+}
+
+
+def _oracle_point_worker(args):
+    """One quadrature point of the oracle's BiCG for a fixed number of iterations (the
+    timing sample); runs in a spawned process with one BLAS thread."""
+    workload, energy_index, j, n_iter = args
+    import time as _t
+    from oracle.bicg import bicg
+    from oracle.contour import ring_contour
+    from oracle.operator import CellOperator
+    from paper_1709_09347_gb300 import synth
+    wl = synth.workload(workload)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    E = float(wl.energies[energy_index])
+    z = ring_contour(wl.lambda_min, wl.n_int)[0][j]
+    t = _t.time()
+    bicg(lambda X: op.apply_P(z, E, X), lambda X: op.apply_P_adjoint(z, E, X), wl.V, wl.V,
+         tol=1e-300, max_iter=n_iter)
+    return _t.time() - t
+
+
+def cpu_baseline_sample(workload: str) -> dict:
+    """The oracle as it stands, on the host's cores: its plain FP64 BiCG (primal + dual,
+    all L columns) runs a fixed number of iterations at one quadrature point per core, in
+    parallel spawned processes; the time per iteration is scaled by the BiCG iteration
+    counts of the oracle's own stored run of that energy (per point, the slowest column)
+    to one energy's Step 1 (extraction excluded).  The sampled energy is the cheapest of
+    the workload's range: the rate is an upper bound for the oracle on the whole step."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import numpy as np
+    if workload not in CPU_SAMPLE:
+        return {"error": f"no stored oracle run to scale a sample of {workload}"}
+    e_idx, path, n_iter = CPU_SAMPLE[workload]
+    g = np.load(os.path.join(ROOT, path))
+    iters = g["iters"] if "iters" in g.files else g[f"iters_{e_idx}"]
+    cores = os.cpu_count() or 1
+    n_int = iters.shape[0]
+    pts = list(range(min(cores, n_int)))
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    try:
+        with cf.ProcessPoolExecutor(max_workers=len(pts), mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(_oracle_point_worker, [(workload, e_idx, j, 1) for j in pts]))   # warm
+            t0 = time.time()
+            times = list(ex.map(_oracle_point_worker, [(workload, e_idx, j, n_iter) for j in pts]))
+            wall = time.time() - t0
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    per_iter_point = float(np.median(times)) / n_iter          # seconds, one core
+    point_iters = iters.max(axis=1)                            # [n_int]
+    # the energy's n_int points spread over `cores` workers, each point to its own count
+    seconds = per_iter_point * float(point_iters.sum()) / len(pts)
+    return {"value": 1.0 / seconds, "unit": UNIT, "cores": len(pts), "kind": "oracle",
+            "sample": (f"{workload}: oracle BiCG, {n_iter} iterations at each of {len(pts)} "
+                       f"quadrature points in parallel ({wall:.1f} s wall), scaled by the stored "
+                       f"oracle run's per-point iteration counts at energy index {e_idx} "
+                       f"(sum {int(point_iters.sum())} over {n_int} points) to one energy's "
+                       f"solves over {len(pts)} cores; extraction not included; the cheapest "
+                       f"energy of the range"),
+            "seconds_per_energy": seconds}
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle, timed as cpu_baseline_sample does, one sample per
+    step."""
     if rank != 0:
         return
-    steps = []
-    samples = []
+    vals, last = [], None
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline_sample(args.workload, 1, 7)
+        r = cpu_baseline_sample(args.workload)
+        if "error" in r:
+            print(json.dumps({"impl": "reference", "unavailable": r["error"]}), flush=True)
+            return
         if k >= args.warmup:
-            steps.append(1.0 / r["value"])
-            samples.append(r)
-    per_energy = sum(steps) / len(steps)
+            vals.append(r["seconds_per_energy"])
+            last = r
+    per_energy = sum(vals) / len(vals)
     value = 1.0 / per_energy
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_energy * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "sample": "1 of n_int quadrature-point solves per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": samples[-1]["sample"]},
+        "config": {"workload": args.workload, "sample": "timed oracle BiCG iterations, scaled per energy"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                         "sample": last["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -236,22 +289,22 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="c2")
-    ap.add_argument("--energies", type=int, default=0,
-                    help="solve only the first K energies of the workload (profiling runs)")
+    ap.add_argument("--workload", default="c3")
+    ap.add_argument("--energy-index", default="",
+                    help="comma-separated energy indices of one step (default per workload)")
+    ap.add_argument("--form", default="mixed", choices=sorted(FORMS), help="headline form")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--per-energy", action="store_true",
+                    help="also time one FP64 BiCG per (energy, quadrature point)")
+    ap.add_argument("--stop-fraction", type=float, default=1.0,
+                    help="load-balance rule of the paper (0.5 = stop once over half the points converged)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--spmm", action="store_true",
                     help="only time the operator apply (stencil + projector SpMM) and exit")
     ap.add_argument("--spmm-systems", type=int, default=0,
-                    help="systems per SpMM launch (default: all primal and dual systems of a step)")
+                    help="systems per SpMM launch (default: the seed batch of a family, 2 N_int)")
     ap.add_argument("--spmm-dtype", default="c64", choices=["c64", "c128"])
-    ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--no-shift", action="store_true",
-                    help="headline with one BiCG per (energy, quadrature point), as in the paper")
-    ap.add_argument("--no-per-energy", action="store_true",
-                    help="skip the per-energy FP64 comparison run")
-    ap.add_argument("--mixed-steps", type=int, default=1)
-    ap.add_argument("--mixed-warmup", type=int, default=1)
     args = ap.parse_args()
     world, rank, local = _dist()
 
@@ -271,18 +324,21 @@ def main():
     dev = torch.device("cuda", local)
 
     wl = synth.workload(args.workload)
-    energies = wl.energies if args.energies <= 0 else wl.energies[:args.energies]
+    idx = step_energy_indices(wl, args.energy_index)
+    energies = wl.energies[idx]
     n_e = len(energies)
     H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
     Vd = torch.from_numpy(wl.V).to(dev).contiguous()
     # launch shapes of the stencil kernel, tuned once per cell before any timing
-    n_tune = min(64, 2 * wl.n_int * n_e)
+    n_tune = 2 * wl.n_int
     tune = {"c128": cbs.autotune_apply(H, n_tune, wl.L, torch.complex128),
             "c64": cbs.autotune_apply(H, n_tune, wl.L, torch.complex64)}
+    hbm, hbm_src = _peaks()
 
     def spmm(n_sys, dtype_name, iters=20):
-        """Operator apply alone, at the batch shape of a step, timed with CUDA events on
-        torch's current stream (the stream the kernels are launched on)."""
+        """Operator apply alone, at the seed batch shape of a family (the 2 N_int primal and
+        dual systems), timed with CUDA events on torch's current stream (the stream the
+        kernels are launched on)."""
         dt = torch.complex64 if dtype_name == "c64" else torch.complex128
         s = 8 if dtype_name == "c64" else 16
         rng = np.random.default_rng(3)
@@ -302,16 +358,22 @@ def main():
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / iters
         outputs = n_sys * wl.grid.n * wl.L
-        bpo = bytes_per_output(wl, s)
-        hbm, src = _peaks()
+        bpo = apply_bytes_per_output(wl, s)
         r = {"dtype": dtype_name, "systems": n_sys, "columns": wl.L, "ms_per_launch": ms,
              "bytes_per_launch": bpo * outputs, "GB_s": bpo * outputs / (ms / 1e3) / 1e9,
-             "peak_GB_s": hbm, "peak_source": src,
+             "peak_GB_s": hbm, "peak_source": hbm_src,
              "frac": bpo * outputs / (ms / 1e3) / 1e9 / hbm,
-             "TFLOP_s": flops_per_output(wl) * outputs / (ms / 1e3) / 1e12}
+             "TFLOP_s": apply_flops_per_output(wl) * outputs / (ms / 1e3) / 1e12,
+             "note": "gather (projector coefficients) + stencil launch pair"}
         del X, Yo, plan
         torch.cuda.empty_cache()
         return r
+
+    if args.spmm:
+        r = spmm(args.spmm_systems or 2 * wl.n_int, args.spmm_dtype)
+        if rank == 0:
+            print(json.dumps({"spmm": r, "workload": args.workload, "apply_shape": tune}), flush=True)
+        return
 
     def barrier():
         if world > 1:
@@ -324,14 +386,19 @@ def main():
             return float(t.item())
         return x
 
-    def one_step(precision, shift=False, profile=True):
-        o = cbs.options(precision=precision, tol=wl.tol, delta=wl.delta, profile=1 if profile else 0,
-                        multi_shift=1 if shift else 0)
-        return cbs.solve(H, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, Vd, o)
+    def options(form, profile=True):
+        f = FORMS[form]
+        return cbs.options(precision=f["precision"], multi_shift=f["multi_shift"], tol=wl.tol,
+                           delta=wl.delta, profile=1 if profile else 0,
+                           stop_fraction=args.stop_fraction)
 
-    def timed(precision, steps, warmup, shift=False):
+    def one_step(form, V=None):
+        return cbs.solve(H, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, Vd if V is None else V,
+                         options(form))
+
+    def timed(form, steps, warmup):
         for _ in range(warmup):
-            one_step(precision, shift)
+            one_step(form)
         barrier()
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -340,7 +407,7 @@ def main():
         with ClockSampler(local) as clk:
             ev0.record()
             for _ in range(steps):
-                results.append(one_step(precision, shift))
+                results.append(one_step(form))
             ev1.record()
             torch.cuda.synchronize()
         launches = cbs.kernel_launches() - l0
@@ -348,74 +415,54 @@ def main():
         ms = max_over_ranks(ev0.elapsed_time(ev1))
         return ms, results, clk.summary(), launches
 
-    hbm, hbm_src = _peaks()
-    sha = _apply_sha()
-    n_step_sys = 2 * wl.n_int * n_e
-    if args.spmm:
-        r = spmm(args.spmm_systems or n_step_sys, args.spmm_dtype)
-        if rank == 0:
-            print(json.dumps({"spmm": r, "workload": args.workload, "apply_shape": tune}), flush=True)
-        return
-
-    def roofline_for(results, precision, ms_total):
-        key = "c64" if precision == "fp32_refine" else "c128"
-        p = {f: sum(r.profile[key][f] for r in results) for f in ("ms", "launches", "outputs")}
-        if not p["ms"]:
-            return None
-        s = 8 if key == "c64" else 16
-        rl = {"kernel": f"k_apply_zm + k_proj_gather ({'complex64' if s == 8 else 'complex128'}): "
-                        "stencil + projector operator apply",
-              "outputs": p["outputs"], "launches": p["launches"],
-              "avg_launch_ms": p["ms"] / max(p["launches"], 1),
-              "share_of_step": p["ms"] / ms_total if ms_total else None}
-        traffic = None
-        tkey = f"{key}_bytes_per_output"
-        if APPLY_TRAFFIC["sha"] == sha and APPLY_TRAFFIC.get(tkey):
-            traffic = APPLY_TRAFFIC[tkey] * p["outputs"] / max(p["launches"], 1)
-        if key == "c64":
-            bpo = bytes_per_output(wl, 8)
-            ach = p["outputs"] * bpo / (p["ms"] / 1e3) / 1e9
-            rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
-                      traffic=traffic, peak_source=hbm_src, bytes_per_output=bpo,
-                      bytes_per_launch=bpo * p["outputs"] / max(p["launches"], 1))
-        else:
-            fpo = flops_per_output(wl)
-            ach = p["outputs"] * fpo / (p["ms"] / 1e3) / 1e12
-            ipo = fp64_instr_per_output(wl)
-            pipe = ipo * p["outputs"] / (p["ms"] / 1e3) / (FP64_FMA_MEASURED_TFLOPS * 1e12 / 2)
-            rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                      frac=ach / FP64_PEAK_TFLOPS, traffic=traffic,
-                      peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
-                      flops_per_output=fpo, flops_per_launch=fpo * p["outputs"] / max(p["launches"], 1),
-                      fp64_instr_per_output=ipo, fp64_pipe_frac_of_measured=pipe,
-                      measured_fp64_fma_tflops=FP64_FMA_MEASURED_TFLOPS)
-        return rl
-
-    def roofline_shift_update(results):
-        """Roofline of the shifted-family update kernel.  Per (energy, point, column) triple
-        and grid point it issues 16 FP64 FMAs (two complex multiply-adds, primal and dual)
-        and moves the scaled direction and the solution in and out, primal and dual
-        (8 x 16 B; the seed residual it also reads is shared by all energies of a point and
-        not counted).  FP64 issue binds first on this part, so the FP64 rate is the roofline
-        and the HBM rate is reported beside it."""
-        p = {f: sum(r.profile["shift_update"][f] for r in results) for f in ("ms", "launches", "outputs")}
-        if not p["ms"]:
-            return None
-        bpo, ipo = 8 * 16, 16
-        sec = p["ms"] / 1e3
-        ach = p["outputs"] * 2 * ipo / sec / 1e12
-        gbs = p["outputs"] * bpo / sec / 1e9
-        return {"kernel": "k_ms_update: shifted-family direction and solution update",
-                "outputs": p["outputs"], "launches": p["launches"],
-                "avg_launch_ms": p["ms"] / max(p["launches"], 1), "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
-                "fp64_instr_per_output": ipo,
-                "fp64_pipe_frac_of_measured": ach / FP64_FMA_MEASURED_TFLOPS,
-                "measured_fp64_fma_tflops": FP64_FMA_MEASURED_TFLOPS,
-                "hbm_achieved_GB_s": gbs, "hbm_peak_GB_s": hbm, "hbm_frac": gbs / hbm,
-                "hbm_peak_source": hbm_src, "bytes_per_output": bpo,
-                "bytes_per_launch": bpo * p["outputs"] / max(p["launches"], 1)}
+    def rooflines(results, ms_total, form):
+        """Per kernel class, from the CUDA events the library records around every launch of
+        it inside the BiCG graphs during the timed steps: device time, units processed,
+        algorithmic bytes (or flops) per unit, achieved rate against the peak."""
+        out = {}
+        for key, name in (("c64", "k_proj_gather_c64x2 + k_apply_c64x2: complex64 stencil + projector apply"),
+                          ("c128", "k_proj_gather + k_apply_zm<double>: complex128 stencil + projector apply"),
+                          ("shift_update", "k_ms_update: shifted-family direction and solution update")):
+            p = {f: sum(r.profile[key][f] for r in results) for f in ("ms", "launches", "outputs")}
+            if not p["ms"]:
+                continue
+            launches = max(p["launches"], 1)
+            sec = p["ms"] / 1e3
+            rl = {"kernel": name, "units": p["outputs"], "launches": p["launches"],
+                  "avg_launch_ms": p["ms"] / launches, "share_of_step": p["ms"] / ms_total}
+            mixed_family = FORMS[form]["precision"] == "fp32_refine"
+            if key == "c64":
+                bpu = apply_bytes_per_output(wl, 8)
+                ach = p["outputs"] * bpu / sec / 1e9
+                rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                          peak_source=hbm_src, bytes_per_unit=bpu, unit_of_work="complex output",
+                          traffic=_traffic("c64_apply", p["outputs"] / launches))
+            elif key == "c128":
+                fpu = apply_flops_per_output(wl)
+                ach = p["outputs"] * fpu / sec / 1e12
+                rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                          frac=ach / FP64_PEAK_TFLOPS, flops_per_unit=fpu, unit_of_work="complex output",
+                          peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
+                          traffic=_traffic("c128_apply", p["outputs"] / launches))
+            elif mixed_family:
+                # per (energy, point, column) triple and grid point: scaled direction and
+                # solution read and written, primal and dual, complex64 (8 x 8 B)
+                bpu = 64
+                ach = p["outputs"] * bpu / sec / 1e9
+                rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                          peak_source=hbm_src, bytes_per_unit=bpu,
+                          unit_of_work="(energy, point, column) triple x grid point",
+                          traffic=_traffic("c64_shift_update", p["outputs"] / launches))
+            else:
+                # FP64 family: 16 FP64 FMAs per unit, bound by the FP64 pipe
+                ach = p["outputs"] * 32 / sec / 1e12
+                rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                          frac=ach / FP64_PEAK_TFLOPS, flops_per_unit=32, traffic=None,
+                          unit_of_work="(energy, point, column) triple x grid point",
+                          peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
+                          hbm_GB_s=p["outputs"] * 128 / sec / 1e9)
+            out[key] = rl
+        return out
 
     def summary(results):
         last = results[-1]
@@ -423,102 +470,95 @@ def main():
         worst = max([float(np.max(e["residual"])) for e in last.energies if len(e["residual"])] or [0.0])
         return last, kept, worst, sorted({e["flags"] for e in last.energies})
 
-    # headline: FP64, one BiCG Krylov sequence per quadrature point and column shared by
-    # all energies of the step (shifted BiCG), or per-energy BiCG with --no-shift
-    shift = not args.no_shift
-    ms, results, clocks, launches = timed("fp64", args.steps, args.warmup, shift)
+    def lam_agreement(a, b):
+        """Largest relative distance from each eigenvalue of form a to its nearest partner
+        of form b, over the energies where both keep the same count."""
+        worst = 0.0
+        for ea, eb in zip(a.energies, b.energies):
+            if len(ea["lam"]) != len(eb["lam"]) or not len(ea["lam"]):
+                continue
+            d = np.abs(ea["lam"][:, None] - eb["lam"][None, :]).min(axis=1) / np.abs(ea["lam"])
+            worst = max(worst, float(d.max()))
+        return worst
+
+    headline = args.form
+    ms, results, clocks, launches = timed(headline, args.steps, args.warmup)
     value = args.steps * n_e * world / (ms / 1e3)
     last, kept, worst_res, flags = summary(results)
-    roofline = roofline_for(results, "fp64", ms)
-    roofline_update = roofline_shift_update(results) if shift else None
-    if roofline_update is not None:
-        roofline_update["share_of_step"] = (roofline_update["avg_launch_ms"] * roofline_update["launches"]
-                                            / ms)
-        if roofline is None or roofline_update["share_of_step"] > roofline["share_of_step"]:
-            roofline, roofline_update = roofline_update, roofline
+    rl = rooflines(results, ms, headline)
+    ranked = sorted(rl.values(), key=lambda r: -r["share_of_step"])
+    roofline = ranked[0] if ranked else None
+    roofline_second = ranked[1] if len(ranked) > 1 else None
 
-    # comparison: the paper's scheme, one FP64 BiCG per (energy, quadrature point)
-    per_energy = None
-    if shift and not args.no_per_energy:
-        msp, resp, clocksp, launchesp = timed("fp64", 1, 1, False)
-        lastp, keptp, worstp, flagsp = summary(resp)
-        per_energy = {"value": n_e * world / (msp / 1e3), "unit": UNIT, "ms_per_step": msp,
-                      "steps": 1, "warmup": 1, "dtype": "f64", "kept_per_energy": keptp,
-                      "same_count_as_headline": keptp == kept, "max_residual": worstp,
-                      "flags": flagsp, "roofline": roofline_for(resp, "fp64", msp),
-                      "clocks": clocksp, "gpu_launches": launchesp,
-                      "stage_ms_last_step": {"solve": lastp.ms_solve, "moments": lastp.ms_moments,
-                                             "extract": lastp.ms_extract}}
-
-    # comparison: complex64 BiCG with FP64 reliable updates on the same workload
-    mixed = None
-    if not args.no_mixed:
-        ms32, res32, clocks32, launches32 = timed("fp32_refine", args.mixed_steps, args.mixed_warmup)
-        last32, kept32, worst32, flags32 = summary(res32)
-        mixed = {"value": args.mixed_steps * n_e * world / (ms32 / 1e3), "unit": UNIT,
-                 "ms_per_step": ms32 / args.mixed_steps, "steps": args.mixed_steps,
-                 "warmup": args.mixed_warmup, "dtype": "c64 BiCG + f64 reliable updates",
-                 "kept_per_energy": kept32, "same_count_as_headline": kept32 == kept,
-                 "max_residual": worst32, "flags": flags32,
-                 "roofline": roofline_for(res32, "fp32_refine", ms32), "clocks": clocks32,
-                 "gpu_launches": launches32,
-                 "stage_ms_last_step": {"solve": last32.ms_solve, "moments": last32.ms_moments,
-                                        "extract": last32.ms_extract}}
+    compare = {}
+    other = [f for f in ("fp64", "mixed") if f != headline]
+    if args.per_energy and headline != "fp64_per_energy":
+        other.append("fp64_per_energy")
+    if not args.no_compare:
+        for form in other:
+            msc, resc, clkc, lc = timed(form, 1, 0)
+            lastc, keptc, worstc, flagsc = summary(resc)
+            compare[form] = {
+                "value": n_e * world / (msc / 1e3), "unit": UNIT, "ms_per_step": msc, "steps": 1,
+                "warmup": 0, "dtype": FORMS[form]["dtype"], "kept_per_energy": keptc,
+                "same_count_as_headline": keptc == kept, "max_residual": worstc, "flags": flagsc,
+                "max_rel_lambda_diff_to_headline": lam_agreement(lastc, last),
+                "headline_speedup": (value / (n_e * world / (msc / 1e3))),
+                "rooflines": rooflines(resc, msc, form), "clocks": clkc, "gpu_launches": lc,
+                "stage_ms": {"solve": lastc.ms_solve, "moments": lastc.ms_moments, "extract": lastc.ms_extract}}
 
     # end to end through the C ABI with host buffers: Hamiltonian upload, V upload,
     # solve, results (eigenvalues, k, residuals, eigenvectors) back to the host
-    def e2e_step():
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         Hh = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
         cbs.set_apply_shape(Hh, torch.complex128, tune["c128"]["py"], tune["c128"]["pz"])
-        r = cbs.solve(Hh, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
-                      cbs.options(precision="fp64", tol=wl.tol, delta=wl.delta,
-                                  multi_shift=1 if shift else 0))
+        cbs.set_apply_shape(Hh, torch.complex64, tune["c64"]["py"], tune["c64"]["pz"], tune["c64"]["x2"])
+        r_e2e = cbs.solve(Hh, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V, options(headline, False))
         Hh.close()
-        return r
-    e2e_steps = 1
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        r_e2e = e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    h2d = wl.vloc.nbytes + wl.V.nbytes
-    if wl.projectors is not None:
-        P = wl.projectors
-        h2d += P.sup_ptr.nbytes + P.sup_idx.nbytes + P.sup_wrap.nbytes + P.sup_val.nbytes + P.h.nbytes
-    d2h = sum(e["lam"].nbytes + e["k"].nbytes + e["residual"].nbytes + e["vectors"].nbytes
-              for e in r_e2e.energies)
-    e2e = {"value": e2e_steps * n_e * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        h2d = wl.vloc.nbytes + wl.V.nbytes
+        if wl.projectors is not None:
+            P = wl.projectors
+            h2d += P.sup_ptr.nbytes + P.sup_idx.nbytes + P.sup_wrap.nbytes + P.sup_val.nbytes + P.h.nbytes
+        d2h = sum(e["lam"].nbytes + e["k"].nbytes + e["residual"].nbytes + e["vectors"].nbytes
+                  for e in r_e2e.energies)
+        e2e = {"value": n_e * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": 1,
+               "same_count_as_headline": [len(e["lam"]) for e in r_e2e.energies] == kept}
 
-    spmm_res = {"c64": spmm(n_step_sys, "c64"), "c128": spmm(n_step_sys, "c128", iters=3)}
+    spmm_res = {"c64": spmm(2 * wl.n_int, "c64"), "c128": spmm(2 * wl.n_int, "c128", iters=3)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline_sample(args.workload, 1, 7)
+            cpu = cpu_baseline_sample(args.workload)
         except Exception as ex:  # noqa: BLE001
             cpu = {"error": str(ex)[-300:]}
 
     if rank == 0:
+        f = FORMS[headline]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {wl.grid.nx}x{wl.grid.ny}x{wl.grid.nz} cell, "
-                                   f"FD{wl.grid.fd_order}, "
-                                   f"{wl.projectors.n_atoms if wl.projectors else 0} atoms x 4 projectors, "
-                                   f"{n_e} energies, N_int={wl.n_int}, L={wl.L}, M={wl.M}, "
-                                   f"lambda_min={wl.lambda_min}, BiCG tol {wl.tol:g}",
-                       "solver": "shifted-family BiCG (one Krylov sequence per z_j for all energies)"
-                                 if shift else "one BiCG per (energy, z_j)",
-                       "energies_per_step": n_e, "l2": "state per step >> L2 (no flush needed)",
+            "scaling": "weak", "vs_baseline": None, "dtype": f["dtype"], "data": "synthetic",
+            "config": {"workload": (f"{args.workload}: {wl.grid.nx}x{wl.grid.ny}x{wl.grid.nz} cell, "
+                                    f"FD{wl.grid.fd_order}, "
+                                    f"{wl.projectors.n_atoms if wl.projectors else 0} atoms x 4 projectors, "
+                                    f"{n_e} of its {len(wl.energies)} energies per step (indices {idx}), "
+                                    f"N_int={wl.n_int}, L={wl.L}, M={wl.M}, lambda_min={wl.lambda_min}, "
+                                    f"BiCG tol {wl.tol:g}"),
+                       "form": headline, "solver": FORMS[headline],
+                       "energies": [float(x) for x in energies], "energies_per_step": n_e,
+                       "stop_fraction": args.stop_fraction,
+                       "l2": "state per step >> L2 (no flush needed)",
                        "kept_per_energy": kept, "max_residual": worst_res, "flags": flags,
                        "apply_shape": tune},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
-            "roofline_second_kernel": roofline_update,
-            "cpu_baseline": cpu, "fp64_per_energy": per_energy, "fp32_refine": mixed,
+            "roofline_second_kernel": roofline_second, "cpu_baseline": cpu, "compare": compare,
             "spmm": spmm_res,
             "stage_ms_last_step": {"solve": last.ms_solve, "moments": last.ms_moments,
                                    "extract": last.ms_extract, "extract_svd": last.ms_svd,

@@ -53,7 +53,11 @@ typedef enum {
   CBS_WRANK = 7        /* warning: numerical rank == L*M, eigenvalues may be missing */
 } cbs_status;
 
-enum { CBS_FP64 = 0, CBS_FP32_REFINE = 1 };     /* cbs_options.precision  */
+/* cbs_options.precision: CBS_FP64 plain FP64 BiCG; CBS_FP32_REFINE complex64 BiCG with FP64
+ * reliable updates (residual replacement); CBS_FP64_APPLY32 FP64 BiCG vectors and
+ * recurrences with the operator applied in complex64 (FP32 accumulation), the true residual
+ * checked with the FP64 operator and the columns above tol continued the same way. */
+enum { CBS_FP64 = 0, CBS_FP32_REFINE = 1, CBS_FP64_APPLY32 = 2 };
 enum { CBS_HANKEL = 0, CBS_RR = 1 };            /* cbs_options.extraction */
 enum { CBS_C128 = 0, CBS_C64 = 1 };             /* element type of vector blocks */
 
@@ -94,7 +98,7 @@ typedef struct {
   double delta;         /* rank cut: keep sigma_i >= delta * sigma_1 (1e-10)              */
   double rho_max;       /* keep eigenpairs with residual rho <= rho_max (1e-8)           */
   int max_iter;         /* BiCG iterations per column (FP64) / per inner solve (20000)   */
-  int precision;        /* CBS_FP64 or CBS_FP32_REFINE                                   */
+  int precision;        /* CBS_FP64, CBS_FP32_REFINE or CBS_FP64_APPLY32 (see above)     */
   int extraction;       /* CBS_HANKEL (Algorithm 1) or CBS_RR (Rayleigh-Ritz)            */
   int check_every;      /* BiCG iterations per CUDA-graph replay between host polls (8)  */
   double inner_tol;     /* complex64 phase ends when ||r|| < inner_tol * max ||r|| since the
@@ -105,12 +109,28 @@ typedef struct {
                            left are finished by FP64 BiCG (12)                             */
   int energies_per_batch; /* energies solved together; 0 = as many as fit (0)            */
   int profile;          /* 1: time every operator-apply launch with CUDA events (0)      */
-  int multi_shift;      /* 1 (CBS_FP64 only): one BiCG Krylov sequence per quadrature point
-                           and column serves every energy of a batch, since
+  int multi_shift;      /* 1: one BiCG Krylov sequence per quadrature point and column
+                           serves every energy of a batch, since
                            P(z, E) = P(z, E0) + (E - E0) I (shifted BiCG; not in the paper);
-                           columns whose true residual misses tol are finished by plain
-                           BiCG from the shifted solution.  0: one BiCG per system (0)     */
+                           columns whose true residual misses tol are then refined per
+                           energy from the shifted solution (FP64 BiCG with CBS_FP64; with
+                           CBS_FP32_REFINE the family runs in complex64 down to family_tol and
+                           the refinement is complex64 BiCG with FP64 reliable updates).
+                           0: one BiCG per system (0)                                       */
   void *stream;         /* cudaStream_t to run on; NULL = the library's own stream       */
+  double family_tol;    /* CBS_FP32_REFINE with multi_shift: relative residual at which an
+                           energy leaves the complex64 family for its refinement
+                           (0 = 1e-6; never below tol)                                      */
+  double stop_fraction; /* load-balance rule of §3.3: once more than
+                           floor(stop_fraction * n_int) quadrature points of an energy have
+                           converged, BiCG stops at its other points (their columns get flag
+                           bit 6 and are not refined).  Applies to cbs_solve with plain FP64
+                           BiCG or with multi_shift.  1.0 = off (1.0; the paper uses 0.5)  */
+  int points_per_wave;  /* quadrature points solved together; the moments are accumulated
+                           wave by wave, so the solver state of only one wave is held at a
+                           time (the rule above then counts the points of one wave).
+                           0 = all points when one energy's fit in memory, else as many as
+                           fit (0)                                                          */
 } cbs_options;
 
 /* Fill *opt with the defaults given above. */
@@ -126,6 +146,14 @@ cbs_status cbs_options_default(cbs_options *opt);
 cbs_status cbs_create_hamiltonian(const cbs_grid *grid, const double *v_loc,
                                   const cbs_projectors *proj, cbs_hamiltonian **out);
 void cbs_hamiltonian_free(cbs_hamiltonian *h);
+
+/* Replaces the local potential of h (§2: V_loc on the diagonal of H0) in place:
+ * v_loc: N doubles, HOST or DEVICE pointer (detected).  The single-precision copy and the
+ * Frobenius norms are recomputed on the device; the projector table and launch shapes are
+ * kept.  A non-finite value returns CBS_EINVAL and leaves h unchanged.  Synchronises the
+ * device; must not run concurrently with other work that uses h.  Lets a caller that
+ * differentiates with respect to V_loc (cbs_objective) keep V_loc on the device. */
+cbs_status cbs_hamiltonian_set_vloc(cbs_hamiltonian *h, const double *v_loc);
 
 /* N = nx*ny*nz of the cell. */
 int64_t cbs_hamiltonian_size(const cbs_hamiltonian *h);
@@ -160,12 +188,17 @@ cbs_status cbs_apply_ws(const cbs_hamiltonian *h, int n_sys, const double *z, co
  * that cannot afford cudaMalloc/cudaFree, which synchronise the device and stall other
  * streams.  This call allocates nothing: its scratch (twists, energies and the projector
  * coefficients) is a fixed 32 MiB array compiled into the library, present on every GPU
- * that loads it until the process exits.  The paper has no counterpart to this entry point.
+ * that loads the library's device code until the process exits.  The paper has no
+ * counterpart to this entry point.
  * z, E: HOST arrays [n_sys]; X, Y: DEVICE [n_sys][N][L] of type dtype; runs on `stream`
- * and does not synchronise.  Sizes whose scratch (about n_sys*L*n_atoms*4*16 bytes in
- * complex128, half that in complex64) exceed the 32 MiB return CBS_EINVAL.  The first call
- * on a device looks up the array's device address (with that device current); make that
- * first call before any stream capture.  All calls share the one array: calls whose GPU
+ * and does not synchronise.  L as for cbs_apply, checked before anything is queued.  Sizes
+ * whose scratch (about n_sys*L*n_atoms*4*16 bytes in complex128, half that in complex64)
+ * exceed the 32 MiB return CBS_EINVAL.  The first call on a device looks up the array's
+ * device address (with that device current); under CUDA's lazy module loading (the
+ * default) that first call is also when the 32 MiB are reserved on the device, so make it
+ * before a memory pool takes the device's free memory, and before any stream capture.  The
+ * looked-up address is kept per device ordinal and is invalid after a device reset
+ * (cudaDeviceReset).  All calls share the one array: calls whose GPU
  * work overlaps (on different streams or threads) race and must be serialised by the
  * caller. */
 cbs_status cbs_apply_noalloc(const cbs_hamiltonian *h, int n_sys, const double *z, const double *E,
@@ -246,7 +279,8 @@ typedef struct {
   int max_iters;        /* largest BiCG iteration count over the energy's systems      */
   int sweeps;           /* FP64 refinement sweeps (0 for plain FP64)                   */
   int flags;            /* bit 0: not converged, bit 1: breakdown, bit 2: rank saturated,
-                           bit 3/4: SVD/eigen-solver iteration limit, bit 5: FP64 continuation */
+                           bit 3/4: SVD/eigen-solver iteration limit, bit 5: FP64 continuation,
+                           bit 6: some points stopped by the load-balance rule (stop_fraction) */
   double sigma_max, sigma_cut; /* sigma_1 and the smallest kept singular value          */
   double max_solve_residual;   /* max over systems/columns of ||V - P(z)Y||/||V|| (FP64) */
 } cbs_stats;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libcbs.so")
 CBS_OK, CBS_EINVAL, CBS_ENOMEM, CBS_ECUDA, CBS_ENOCONV, CBS_EBREAKDOWN, CBS_ETIMEOUT, CBS_WRANK = range(8)
 STATUS_NAMES = ["CBS_OK", "CBS_EINVAL", "CBS_ENOMEM", "CBS_ECUDA", "CBS_ENOCONV",
                 "CBS_EBREAKDOWN", "CBS_ETIMEOUT", "CBS_WRANK"]
-CBS_FP64, CBS_FP32_REFINE = 0, 1
+CBS_FP64, CBS_FP32_REFINE, CBS_FP64_APPLY32 = 0, 1, 2
 CBS_HANKEL, CBS_RR = 0, 1
 CBS_C128, CBS_C64 = 0, 1
 
@@ -29,7 +29,7 @@ EXPORTS = (
     "cbs_result_timing", "cbs_result_profile", "cbs_result_free", "cbs_last_error",
     "cbs_kernel_launches", "cbs_apply_workspace_size", "cbs_apply_ws", "cbs_apply_noalloc",
     "cbs_objective", "cbs_autotune_apply", "cbs_set_apply_shape",
-    "cbs_result_extract_timing",
+    "cbs_result_extract_timing", "cbs_hamiltonian_set_vloc",
 )
 
 
@@ -55,7 +55,8 @@ class Options(ct.Structure):
                 ("max_iter", ct.c_int), ("precision", ct.c_int), ("extraction", ct.c_int),
                 ("check_every", ct.c_int), ("inner_tol", ct.c_double), ("max_sweeps", ct.c_int), ("inner_max_iter", ct.c_int), ("stall_sweeps", ct.c_int),
                 ("energies_per_batch", ct.c_int), ("profile", ct.c_int), ("multi_shift", ct.c_int),
-                ("stream", ct.c_void_p)]
+                ("stream", ct.c_void_p), ("family_tol", ct.c_double), ("stop_fraction", ct.c_double),
+                ("points_per_wave", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -88,6 +89,7 @@ def load():
     lib.cbs_create_hamiltonian.argtypes = [P(Grid), P(D), P(Projectors), P(V)]
     lib.cbs_hamiltonian_free.argtypes = [V]
     lib.cbs_hamiltonian_free.restype = None
+    lib.cbs_hamiltonian_set_vloc.argtypes = [V, V]
     lib.cbs_hamiltonian_size.argtypes = [V]
     lib.cbs_hamiltonian_size.restype = ct.c_int64
     lib.cbs_hamiltonian_norms.argtypes = [V, D, P(D), P(D), P(D)]
@@ -134,7 +136,7 @@ def options(**kw) -> Options:
     load().cbs_options_default(ct.byref(o))
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
-            v = {"fp64": CBS_FP64, "fp32_refine": CBS_FP32_REFINE}[v]
+            v = {"fp64": CBS_FP64, "fp32_refine": CBS_FP32_REFINE, "fp64_apply32": CBS_FP64_APPLY32}[v]
         if k == "extraction" and isinstance(v, str):
             v = {"hankel": CBS_HANKEL, "rr": CBS_RR}[v]
         setattr(o, k, v)
@@ -168,6 +170,22 @@ class Hamiltonian:
     @property
     def handle(self):
         return self._h
+
+    def set_vloc(self, vloc):
+        """Replace V_loc in place (cbs_hamiltonian_set_vloc): a numpy array or a CUDA float64
+        tensor of N values."""
+        if isinstance(vloc, np.ndarray):
+            v = np.ascontiguousarray(vloc, dtype=np.float64)
+            ptr = ct.c_void_p(v.ctypes.data)
+        else:
+            import torch
+            assert vloc.is_cuda and vloc.dtype == torch.float64 and vloc.is_contiguous()
+            torch.cuda.current_stream().synchronize()
+            v = vloc
+            ptr = ct.c_void_p(vloc.data_ptr())
+        count = v.numel() if hasattr(v, "numel") else v.size
+        assert count == self.n, "V_loc must have N values"
+        _check(load().cbs_hamiltonian_set_vloc(self._h, ptr))
 
     def norms(self, E):
         a, b, c = ct.c_double(), ct.c_double(), ct.c_double()
@@ -349,41 +367,67 @@ class ApplyPlan:
 
 
 def objective(H: Hamiltonian, E, lambda_min, n_int, L, M, V, opts: Options | None = None,
-              grad: bool = False):
+              grad: bool = False, grad_out=None):
     """J = sum_c sum_j c_j ||Y_j||_F^2 of the ring solves at energy E (cbs_objective); with
-    grad=True also (dJ/dV_loc as a numpy array [N], dJ/dE)."""
+    grad=True also (dJ/dV_loc, dJ/dE).  dJ/dV_loc is a numpy array [N], or is written into
+    grad_out (a CUDA float64 tensor [N]) when given."""
     lib = load()
     ctr = Contour(float(lambda_min), int(n_int))
     Vh = np.ascontiguousarray(V, dtype=np.complex128)
     o = opts or options()
     J = ct.c_double()
     gE = ct.c_double()
-    gV = np.zeros(H.n) if grad else None
+    gV = None
+    gptr = None
+    if grad:
+        if grad_out is not None:
+            import torch
+            assert grad_out.is_cuda and grad_out.dtype == torch.float64 and grad_out.numel() == H.n
+            gV = grad_out
+            gptr = ct.cast(ct.c_void_p(grad_out.data_ptr()), ct.POINTER(ct.c_double))
+        else:
+            gV = np.zeros(H.n)
+            gptr = _dptr(gV)
     _check(lib.cbs_objective(H.handle, float(E), ct.byref(ctr), int(L), int(M), ct.c_void_p(Vh.ctypes.data),
-                             ct.byref(o), ct.byref(J), _dptr(gV) if grad else None,
-                             ct.byref(gE) if grad else None))
+                             ct.byref(o), ct.byref(J), gptr, ct.byref(gE) if grad else None))
     return (J.value, gV, gE.value) if grad else J.value
 
 
 def ring_objective(vloc, E, grid, projectors, lambda_min, n_int, L, M, V, opts: Options | None = None):
     """Differentiable J(V_loc, E): a torch.autograd.Function whose backward runs the adjoint
-    solves on the device (the forward solutions are recomputed, not stored)."""
+    solves on the device (the forward solutions are recomputed, not stored).  With V_loc a
+    CUDA float64 tensor it stays on the device: the Hamiltonian is built once and its
+    potential replaced in place (cbs_hamiltonian_set_vloc), and the gradient is written
+    straight into a device tensor."""
     import torch
+
+    state = {}
+
+    def ham(v):
+        if "H" not in state:
+            state["H"] = Hamiltonian(grid, np.zeros(grid.nx * grid.ny * grid.nz), projectors)
+        H = state["H"]
+        H.set_vloc(v.detach().contiguous() if v.is_cuda else v.detach().cpu().numpy())
+        return H
 
     class _RingObjective(torch.autograd.Function):
         @staticmethod
         def forward(ctx, v, e):
-            H = Hamiltonian(grid, v.detach().cpu().numpy(), projectors)
-            J = objective(H, float(e), lambda_min, n_int, L, M, V, opts)
+            J = objective(ham(v), float(e), lambda_min, n_int, L, M, V, opts)
             ctx.save_for_backward(v, e)
             return torch.tensor(J, dtype=torch.float64, device=v.device)
 
         @staticmethod
         def backward(ctx, gJ):
             v, e = ctx.saved_tensors
-            H = Hamiltonian(grid, v.detach().cpu().numpy(), projectors)
-            _, gV, gE = objective(H, float(e), lambda_min, n_int, L, M, V, opts, grad=True)
-            gv = torch.from_numpy(gV).to(v.device, v.dtype) * gJ
+            H = ham(v)
+            if v.is_cuda:
+                g = torch.empty(H.n, dtype=torch.float64, device=v.device)
+                _, gv, gE = objective(H, float(e), lambda_min, n_int, L, M, V, opts, grad=True, grad_out=g)
+            else:
+                _, gVh, gE = objective(H, float(e), lambda_min, n_int, L, M, V, opts, grad=True)
+                gv = torch.from_numpy(gVh)
+            gv = gv.to(v.dtype) * gJ
             ge = torch.tensor(gE, dtype=e.dtype, device=e.device) * gJ
             return gv, ge
 

@@ -51,6 +51,9 @@ extern "C" cbs_status cbs_options_default(cbs_options *o) {
   o->energies_per_batch = 0;
   o->multi_shift = 0;
   o->stream = nullptr;
+  o->family_tol = 0.0;
+  o->stop_fraction = 1.0;
+  o->points_per_wave = 0;
   return CBS_OK;
 }
 
@@ -61,6 +64,7 @@ extern "C" cbs_status cbs_apply(const cbs_hamiltonian *h, int n_sys, const doubl
     return CBS_EINVAL;
   }
   if (dtype != CBS_C128 && dtype != CBS_C64) { set_error("cbs_apply: dtype"); return CBS_EINVAL; }
+  if (!apply_supported(h->v, L, dtype, "cbs_apply")) return CBS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const HamView &H = h->v;
   const size_t csz = dtype == CBS_C128 ? sizeof(double2) : sizeof(float2);
@@ -105,6 +109,7 @@ extern "C" cbs_status cbs_apply_ws(const cbs_hamiltonian *h, int n_sys, const do
     return CBS_EINVAL;
   }
   if (dtype != CBS_C128 && dtype != CBS_C64) { set_error("cbs_apply_ws: dtype"); return CBS_EINVAL; }
+  if (!apply_supported(h->v, L, dtype, "cbs_apply_ws")) return CBS_EINVAL;
   if (workspace_bytes < cbs_apply_workspace_size(h, n_sys, L, dtype)) {
     set_error("cbs_apply_ws: workspace smaller than cbs_apply_workspace_size");
     return CBS_EINVAL;

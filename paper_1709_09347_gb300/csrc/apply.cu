@@ -343,18 +343,36 @@ __global__ void __launch_bounds__(256) k_apply_zm(HamView H, int L, const typena
   }
 }
 
-// Complex64 fast path: each thread owns two adjacent columns of one (x, y) line, so every
-// load and store is 16 bytes; z arms from the register queue of Bloch-extended values;
-// the projector scatter reads one packed (atom, wrap) word, one float4 of projector values
-// and 64 bytes of D per covering entry (D laid out [system][atom][column][4]).
+// Asynchronous 16-byte global -> shared copies (cp.async, bypassing L1), used to keep
+// several planes of X in flight per thread.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
+// Planes of X a thread of the complex64 stencil keeps in flight ahead of the one it needs.
+// The z-march consumes one 16-byte value per thread and plane; without a prefetch each
+// plane waits out a full DRAM latency, which bounded the kernel at ~20% of HBM bandwidth.
+constexpr int kApplyPF = 6;
+
+// Complex64 fast path: each thread owns two adjacent columns of one (x, y) line, so every
+// load and store is 16 bytes; z arms from the register queue of Bloch-extended values, fed
+// from a per-thread ring of kApplyPF planes in shared memory filled by cp.async; the
+// projector scatter reads one packed (atom, wrap) word, one float4 of projector values and
+// 64 bytes of D per covering entry (D laid out [system][atom][column][4]).  The point's
+// scatter-table range and local potential are loaded one plane ahead.
 template <bool PER_COL, int MH>
-__global__ void __launch_bounds__(256, 3) k_apply_c64x2(HamView H, int L, const float4 *__restrict__ X,
+__global__ void __launch_bounds__(256, 2) k_apply_c64x2(HamView H, int L, const float4 *__restrict__ X,
                                                         float4 *__restrict__ Y,
                                                         const double2 *__restrict__ twist,
                                                         const double *__restrict__ E,
                                                         const float4 *__restrict__ D,
                                                         const int *__restrict__ sys_active) {
+  extern __shared__ float4 pf_ring[];   // [kApplyPF][threads of the block]
   const int s = blockIdx.z;
   if (sys_active && !sys_active[s]) return;
   const int t = threadIdx.x;                 // column pair
@@ -362,6 +380,8 @@ __global__ void __launch_bounds__(256, 3) k_apply_c64x2(HamView H, int L, const 
   const int ix = blockIdx.x * blockDim.y + threadIdx.y;
   const int iy = blockIdx.y * blockDim.z + threadIdx.z;   // a block covers blockDim.z rows
   if (ix >= H.nx || iy >= H.ny) return;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nth = blockDim.x * blockDim.y * blockDim.z;
   const int nx = H.nx, ny = H.ny, nz = H.nz, nxy = nx * ny;
   const double2 wd0 = twist[PER_COL ? (int64_t)s * L + 2 * t : s];
   const double2 wd1 = twist[PER_COL ? (int64_t)s * L + 2 * t + 1 : s];
@@ -380,22 +400,48 @@ __global__ void __launch_bounds__(256, 3) k_apply_c64x2(HamView H, int L, const 
   float4 *Ys = Y + (int64_t)s * H.n * L2;
   const float4 *Ds = D + (int64_t)s * H.n_atoms * L * 2 + 4 * t;   // column pair 2t, 2t+1
   const int line = iy * nx + ix;
-  auto bloch = [&](int p) -> float4 {
-    if (p >= nz) return c2mul(w0, w1, Xs[((p - nz) * nxy + line) * L2 + t]);
-    if (p < 0) return c2mul(wi0, wi1, Xs[((p + nz) * nxy + line) * L2 + t]);
-    return Xs[(p * nxy + line) * L2 + t];
+  // address of this thread's value in plane p of the Bloch-extended field, p in [-nz, 2nz)
+  auto src = [&](int p) -> const float4 * {
+    const int pw = p >= nz ? p - nz : (p < 0 ? p + nz : p);
+    return Xs + (pw * nxy + line) * L2 + t;
   };
+  auto bloch = [&](int p) -> float4 {
+    const float4 v = *src(p);
+    if (p >= nz) return c2mul(w0, w1, v);
+    if (p < 0) return c2mul(wi0, wi1, v);
+    return v;
+  };
+  // planes MH .. nz-1+MH enter the queue head one per step; the ring holds the next
+  // kApplyPF of them (one commit group per plane, empty groups past the last plane)
+  const int last = nz - 1 + MH;
+#pragma unroll
+  for (int k = 0; k < kApplyPF; ++k) {
+    if (MH + k <= last) cp_async16(&pf_ring[k * nth + tid], src(MH + k));
+    cp_async_commit();
+  }
   float4 q[2 * MH + 1];
 #pragma unroll
   for (int d = 0; d < 2 * MH; ++d) q[d] = bloch(d - MH);
+  int e0 = 0, e1 = 0;
+  if (D) { e0 = (int)H.pt_ptr[line]; e1 = (int)H.pt_ptr[line + 1]; }
+  float vnext = vl[line];
+  int slot = 0;
   for (int iz = 0; iz < nz; ++iz) {
     const int pt = iz * nxy + line;
-    int e0 = 0, e1 = 0;
-    if (D) { e0 = (int)H.pt_ptr[pt]; e1 = (int)H.pt_ptr[pt + 1]; }
-    q[2 * MH] = bloch(iz + MH);
+    const int ce0 = e0, ce1 = e1;
+    const float vcur = vnext;
+    if (iz + 1 < nz) {                       // next plane's table range and potential
+      if (D) { e0 = (int)H.pt_ptr[pt + nxy]; e1 = (int)H.pt_ptr[pt + nxy + 1]; }
+      vnext = vl[pt + nxy];
+    }
+    cp_async_wait<kApplyPF - 1>();           // plane iz + MH has landed in `slot`
+    {
+      const float4 v = pf_ring[slot * nth + tid];
+      q[2 * MH] = iz + MH >= nz ? c2mul(w0, w1, v) : v;
+    }
     const int b = pt * L2 + t;
     const float4 x0 = q[MH];
-    const float dd = dk + vl[pt];
+    const float dd = dk + vcur;
     float4 acc = make_float4(dd * x0.x, dd * x0.y, dd * x0.z, dd * x0.w);
 #pragma unroll
     for (int k = 1; k <= MH; ++k) {
@@ -408,7 +454,11 @@ __global__ void __launch_bounds__(256, 3) k_apply_c64x2(HamView H, int L, const 
       acc.z += wx * (a1.z + a2.z) + wy * (b1.z + b2.z) + wz * (z1.z + z2.z);
       acc.w += wx * (a1.w + a2.w) + wy * (b1.w + b2.w) + wz * (z1.w + z2.w);
     }
-    for (int qq = e0; qq < e1; ++qq) {
+    // the queue head has been consumed: refill its slot with plane iz + MH + kApplyPF
+    if (iz + MH + kApplyPF <= last) cp_async16(&pf_ring[slot * nth + tid], src(iz + MH + kApplyPF));
+    cp_async_commit();
+    slot = slot + 1 == kApplyPF ? 0 : slot + 1;
+    for (int qq = ce0; qq < ce1; ++qq) {
       const int2 aw = H.pt_aw[qq];
       const float4 p = H.pt_p32[qq];
       const float4 *Da = Ds + (int64_t)aw.x * L * 2;
@@ -426,6 +476,7 @@ __global__ void __launch_bounds__(256, 3) k_apply_c64x2(HamView H, int L, const 
 #pragma unroll
     for (int d = 0; d < 2 * MH; ++d) q[d] = q[d + 1];
   }
+  cp_async_wait<0>();
 }
 
 template <typename R>
@@ -477,8 +528,9 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
   }
   const typename CT<R>::T *Dp = H.n_atoms ? D : nullptr;
   const int ti = sizeof(typename CT<R>::T) == sizeof(float2) ? 1 : 0;
-  // complex64 with an even number of columns and at most 4 projectors: two columns per thread
-  if (ti == 1 && L % 2 == 0 && L <= 512 && H.np4 == 4 && H.tune_x2 >= 0) {
+  // complex64 with an even number of columns and at most 4 projectors: two columns per
+  // thread (the only complex64 kernel that takes more than 256 columns)
+  if (ti == 1 && L % 2 == 0 && L <= 512 && H.np4 == 4 && (H.tune_x2 >= 0 || L > 256)) {
     const int L2 = L / 2;
     int py = 256 / L2, pz = 1;
     if (H.tune_py[1] > 0 && H.tune_pz[1] > 0 && H.tune_py[1] * H.tune_pz[1] * L2 <= 256) {
@@ -491,10 +543,11 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
     const float4 *X4 = reinterpret_cast<const float4 *>(X);
     float4 *Y4 = reinterpret_cast<float4 *>(Y);
     const float4 *D4 = H.n_atoms ? reinterpret_cast<const float4 *>(D) : nullptr;
+    const size_t pf_smem = (size_t)kApplyPF * blk.x * blk.y * blk.z * sizeof(float4);
 #define FX(MH)                                                                                     \
   do {                                                                                             \
-    if (per_col) k_apply_c64x2<true, MH><<<grd, blk, 0, st>>>(H, L, X4, Y4, twist, E, D4, sys_active); \
-    else k_apply_c64x2<false, MH><<<grd, blk, 0, st>>>(H, L, X4, Y4, twist, E, D4, sys_active);    \
+    if (per_col) k_apply_c64x2<true, MH><<<grd, blk, pf_smem, st>>>(H, L, X4, Y4, twist, E, D4, sys_active); \
+    else k_apply_c64x2<false, MH><<<grd, blk, pf_smem, st>>>(H, L, X4, Y4, twist, E, D4, sys_active);    \
     cbs::count_launches(1);                                                                        \
   } while (0)
     switch (H.m) {
@@ -538,6 +591,14 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
 #undef ZM
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
+}
+
+bool apply_supported(const HamView &H, int L, int dtype, const char *who) {
+  const bool ok = L >= 1 && (L <= 256 || (dtype == CBS_C64 && L % 2 == 0 && L <= 512 && H.np4 == 4));
+  if (!ok)
+    set_error(std::string(who) + ": unsupported number of columns L (complex128: 1..256; complex64: "
+              "1..256, or an even L up to 512 when atoms carry at most 4 projectors)");
+  return ok;
 }
 
 template <typename R>

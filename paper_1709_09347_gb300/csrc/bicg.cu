@@ -133,10 +133,13 @@ __global__ void k_dot_pq(int n, int64_t N, int L, int chunk_pts, int n_chunks,
   double acc[4] = {0, 0, 0, 0};
   const int64_t i0 = (int64_t)chunk * chunk_pts;
   const int64_t i1 = min(N, i0 + chunk_pts);
-  R ax = 0, ay = 0;
+  // (p~, q) decides alpha: its products are formed and summed in FP64 also for complex64
+  // vectors (a single-precision sum loses the small inner products of late iterations to
+  // cancellation, which stalls the recurrence)
+  double ax = 0, ay = 0;
   for (int64_t i = i0 + ly; i < i1; i += py) {
-    const C pd = p[((int64_t)(n + s) * N + i) * L + c];
-    const C qq = q[((int64_t)s * N + i) * L + c];
+    const double2 pd = to_d(p[((int64_t)(n + s) * N + i) * L + c]);
+    const double2 qq = to_d(q[((int64_t)s * N + i) * L + c]);
     ax += pd.x * qq.x + pd.y * qq.y;
     ay += pd.x * qq.y - pd.y * qq.x;
   }
@@ -180,7 +183,10 @@ __global__ void k_pass_b(int n, int64_t N, int L, int chunk_pts, int n_chunks,
   const bool act = active[k];
   const C a = from_d<R>(alpha[k]), ac = cconj(a);
   const C na = mk<R>(-a.x, -a.y), nac = mk<R>(-a.x, a.y);
-  R s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  // rho = (r~, r) in FP64 products and sums (it decides beta; see k_dot_pq); the norms,
+  // sums of squares without cancellation, in the working precision
+  double s0 = 0, s1 = 0;
+  R s2 = 0, s3 = 0;
   const int64_t i0 = (int64_t)chunk * chunk_pts;
   const int64_t i1 = min(N, i0 + chunk_pts);
   if (act) {
@@ -192,13 +198,14 @@ __global__ void k_pass_b(int n, int64_t N, int L, int chunk_pts, int n_chunks,
       if (x) x[ed] = cfma(ac, p[ed], x[ed]);
       C rd = cfma(nac, q[ed], r[ed]);
       r[ed] = rd;
-      s0 += rd.x * rr.x + rd.y * rr.y;
-      s1 += rd.x * rr.y - rd.y * rr.x;
+      const double2 r1 = to_d(rr), r2 = to_d(rd);
+      s0 += r2.x * r1.x + r2.y * r1.y;
+      s1 += r2.x * r1.y - r2.y * r1.x;
       s2 += rr.x * rr.x + rr.y * rr.y;
       s3 += rd.x * rd.x + rd.y * rd.y;
     }
   }
-  double acc[4] = {(double)s0, (double)s1, (double)s2, (double)s3};
+  double acc[4] = {s0, s1, (double)s2, (double)s3};
   block_partials<R>(acc, part, (int64_t)s * n_chunks + chunk);
 }
 
@@ -246,6 +253,46 @@ __global__ void k_reduce_beta(int n, int L, int n_chunks, const double *part, do
     sys_active[s] = any;
     sys_active[n + s] = any;
     if (any) atomicAdd(n_active, 1);
+  }
+}
+
+// Load-balance rule of §3.3 (second stopping rule): the systems of one energy are its
+// n_pt quadrature points (systems e * n_pt + j, duals n + s); once more than `need` of them
+// have stopped, the others of that energy are stopped too.  A system counts as stopped when
+// none of its columns is active; the columns stopped by the rule get flag bit 6.
+// One block per energy, one thread per point (n_pt <= 1024).
+__global__ void k_group_stop(int n, int n_pt, int L, int need, int *active, int *flags,
+                             int *sys_active) {
+  const int e = blockIdx.x, j = threadIdx.x;
+  const int s = e * n_pt + j;
+  const int stopped = j < n_pt ? !sys_active[s] : 0;
+  const int count = __syncthreads_count(stopped);
+  if (count <= need || j >= n_pt || stopped) return;
+  for (int c = 0; c < L; ++c) {
+    const int64_t k = (int64_t)s * L + c;
+    if (active[k]) { active[k] = 0; flags[k] |= 64; }
+  }
+  sys_active[s] = 0;
+  sys_active[n + s] = 0;
+}
+
+// The same rule for a shifted family: for energy e, point j counts as stopped when none of
+// its (e, j) columns is active.
+__global__ void k_ms_group_stop(int n_pt, int L, int need, int *sactive, int *sflags, int *siters,
+                                const int *seed_iters) {
+  const int e = blockIdx.x, j = threadIdx.x;
+  int live = 0;
+  if (j < n_pt)
+    for (int c = 0; c < L; ++c) live |= sactive[((int64_t)e * n_pt + j) * L + c];
+  const int count = __syncthreads_count(j < n_pt && !live);
+  if (count <= need || j >= n_pt || !live) return;
+  for (int c = 0; c < L; ++c) {
+    const int64_t kk = ((int64_t)e * n_pt + j) * L + c;
+    if (sactive[kk]) {
+      sactive[kk] = 0;
+      sflags[kk] |= 64;
+      siters[kk] = seed_iters[(int64_t)j * L + c];
+    }
   }
 }
 
@@ -343,11 +390,14 @@ static void chunking(int64_t N, int L, int *chunk_pts, int *n_chunks) {
 }
 
 template <typename R>
-size_t Bicg<R>::bytes_needed(const HamView &H, int n, int L) {
+size_t Bicg<R>::bytes_needed(const HamView &H, int n, int L, bool apply32) {
   int cp, nc;
   chunking(H.n, L, &cp, &nc);
   const int64_t vec = (int64_t)2 * n * H.n * L * sizeof(C);
   int64_t b = 4 * align256(vec);
+  if (apply32)
+    b += 2 * align256((int64_t)2 * n * H.n * L * sizeof(float2)) +
+         align256((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * sizeof(float2));
   b += align256((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * sizeof(C));
   b += align256((int64_t)2 * n * sizeof(double2)) + align256((int64_t)2 * n * sizeof(double));
   b += 4 * align256((int64_t)n * L * sizeof(double2)) + 6 * align256((int64_t)n * L * sizeof(double));
@@ -360,7 +410,7 @@ template <typename R>
 cbs_status Bicg<R>::alloc(const HamView &H_, int n_, int L_) {
   H = H_; n = n_; L = L_; N = H.n;
   chunking(N, L, &chunk_pts, &n_chunks);
-  bytes = bytes_needed(H, n, L);
+  bytes = bytes_needed(H, n, L, apply32);
   cudaError_t e = cudaMalloc(&block, bytes);
   if (e != cudaSuccess) {
     block = nullptr;
@@ -391,6 +441,11 @@ cbs_status Bicg<R>::alloc(const HamView &H_, int n_, int L_) {
   n_active = (int *)take(256);
   part = (double *)take((int64_t)n * n_chunks * L * 4 * sizeof(double));
   sys_apply = (unsigned long long *)take(256);
+  if (apply32) {
+    p32 = (float2 *)take((int64_t)2 * n * N * L * sizeof(float2));
+    q32 = (float2 *)take((int64_t)2 * n * N * L * sizeof(float2));
+    D32 = (float2 *)take((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * sizeof(float2));
+  }
   CBS_CUDA(cudaMemset(sys_apply, 0, sizeof(unsigned long long)));
   return CBS_OK;
 }
@@ -445,6 +500,48 @@ cbs_status Bicg<R>::init(const double2 *B, int64_t bstride, const double2 *Bd, i
   return CBS_OK;
 }
 
+// complex128 <-> complex64 copies of the systems that are still active (per system, over
+// [N][L] blocks)
+__global__ void k_narrow(int64_t per_sys, const double2 *__restrict__ a, float2 *__restrict__ b,
+                         const int *__restrict__ sys_active) {
+  const int s = blockIdx.y;
+  if (sys_active && !sys_active[s]) return;
+  const double2 *as = a + (int64_t)s * per_sys;
+  float2 *bs = b + (int64_t)s * per_sys;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_sys; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = as[i];
+    bs[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+__global__ void k_widen(int64_t per_sys, const float2 *__restrict__ a, double2 *__restrict__ b,
+                        const int *__restrict__ sys_active) {
+  const int s = blockIdx.y;
+  if (sys_active && !sys_active[s]) return;
+  const float2 *as = a + (int64_t)s * per_sys;
+  double2 *bs = b + (int64_t)s * per_sys;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_sys; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = as[i];
+    bs[i] = make_double2(v.x, v.y);
+  }
+}
+
+// q = P(z) p for the 2n systems of a Bicg state: in the state's precision, or (apply32)
+// through complex64 copies
+template <typename R>
+static cbs_status bicg_apply(Bicg<R> &b, const typename CT<R>::T *p, typename CT<R>::T *q, cudaStream_t st) {
+  if (sizeof(R) == sizeof(double) && b.apply32) {
+    const int64_t per = b.N * b.L;
+    dim3 grd((unsigned)std::min<int64_t>(64, (per + 255) / 256), (unsigned)(2 * b.n), 1);
+    k_narrow<<<grd, 256, 0, st>>>(per, (const double2 *)p, b.p32, b.sys_active); cbs::count_launches(1);
+    CBS_CUDA(cudaGetLastError());
+    CBS_TRY_B(apply_P<float>(b.H, 2 * b.n, b.L, b.p32, b.q32, b.tw, false, b.E, b.D32, b.sys_active, st));
+    k_widen<<<grd, 256, 0, st>>>(per, b.q32, (double2 *)q, b.sys_active); cbs::count_launches(1);
+    CBS_CUDA(cudaGetLastError());
+    return CBS_OK;
+  }
+  return apply_P<R>(b.H, 2 * b.n, b.L, p, q, b.tw, false, b.E, b.D, b.sys_active, st);
+}
+
 template <typename R>
 cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st, int kk) {
   dim3 blk = col_block(L);
@@ -454,7 +551,7 @@ cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st, int kk) {
   const bool prof = profile && kk >= 0 && 2 * kk + 1 < n_prof_ev;
   // recorded as real event nodes of the graph (not capture-dependency markers)
   if (prof) CBS_CUDA(cudaEventRecordWithFlags(prof_ev[2 * kk], st, cudaEventRecordExternal));
-  cbs_status s = apply_P<R>(H, 2 * n, L, p, q, tw, false, E, D, sys_active, st);
+  cbs_status s = bicg_apply(*this, p, q, st);
   if (s != CBS_OK) return s;
   if (prof) CBS_CUDA(cudaEventRecordWithFlags(prof_ev[2 * kk + 1], st, cudaEventRecordExternal));
   k_dot_pq<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, p, q, part, sys_active); cbs::count_launches(1);
@@ -469,6 +566,11 @@ cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st, int kk) {
   k_reduce_beta<<<n, L, 0, st>>>(n, L, n_chunks, part, rho, rho_prev, beta, tgt, tgtd, rmax, rmaxd,
                                  tfac, active, iters, flags, max_iter, sys_active, n_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
+  if (group > 0 && group_need < group) {
+    k_group_stop<<<n / group, ((group + 31) / 32) * 32, 0, st>>>(n, group, L, group_need, active, flags, sys_active);
+    cbs::count_launches(1);
+    CBS_CUDA(cudaGetLastError());
+  }
   return CBS_OK;
 }
 
@@ -611,29 +713,32 @@ __global__ void k_ms_coef(int n_pt, int n_sh, int L, const double *sigma, const 
 // p^_e = r + cb p^_e, x_e += ca p^_e (primal; p^_e = pi_e^k p_e, the scaled search
 // direction); conjugated coefficients for the dual.  One block per (chunk of points,
 // quadrature point); every energy of that point reads the same seed residual chunk.
-__global__ void k_ms_update(int n_pt, int n_sh, int64_t N, int L, int chunk_pts, const double2 *r,
-                            double2 *P, double2 *X, const double2 *cb,
-                            const double2 *ca, const int *sactive, const int *seed_sys_active) {
+template <typename R>
+__global__ void k_ms_update(int n_pt, int n_sh, int64_t N, int L, int chunk_pts,
+                            const typename CT<R>::T *__restrict__ r, typename CT<R>::T *__restrict__ P,
+                            typename CT<R>::T *__restrict__ X, const double2 *cb, const double2 *ca,
+                            const int *sactive, const int *seed_sys_active) {
+  typedef typename CT<R>::T C;
   const int j = blockIdx.y, chunk = blockIdx.x, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
   if (!seed_sys_active[j]) return;
   const int64_t n = (int64_t)n_sh * n_pt;
   const int64_t i0 = (int64_t)chunk * chunk_pts;
   const int64_t i1 = min(N, i0 + chunk_pts);
-  const double2 *rp = r + (int64_t)j * N * L, *rd = r + (int64_t)(n_pt + j) * N * L;
+  const C *rp = r + (int64_t)j * N * L, *rd = r + (int64_t)(n_pt + j) * N * L;
   for (int e = 0; e < n_sh; ++e) {
     const int64_t s = (int64_t)e * n_pt + j;
     const int64_t kk = s * L + c;
     if (!sactive[kk]) continue;
-    const double2 b = cb[kk], al = ca[kk];
-    const double2 bc = cconj(b), alc = cconj(al);
-    double2 *Pp = P + s * N * L, *Xp = X + s * N * L;
-    double2 *Pd = P + (n + s) * N * L, *Xd = X + (n + s) * N * L;
+    const C b = from_d<R>(cb[kk]), al = from_d<R>(ca[kk]);
+    const C bc = cconj(b), alc = cconj(al);
+    C *Pp = P + s * N * L, *Xp = X + s * N * L;
+    C *Pd = P + (n + s) * N * L, *Xd = X + (n + s) * N * L;
     for (int64_t i = i0 + ly; i < i1; i += py) {
       const int64_t o = i * L + c;
-      const double2 pv = cfma(b, Pp[o], rp[o]);
+      const C pv = cfma(b, Pp[o], rp[o]);
       Pp[o] = pv;
       Xp[o] = cfma(al, pv, Xp[o]);
-      const double2 pdv = cfma(bc, Pd[o], rd[o]);
+      const C pdv = cfma(bc, Pd[o], rd[o]);
       Pd[o] = pdv;
       Xd[o] = cfma(alc, pdv, Xd[o]);
     }
@@ -701,21 +806,23 @@ __global__ void k_ms_reduce_beta(int n_pt, int n_sh, int L, int n_chunks, const 
   }
 }
 
-size_t MultiShift::bytes_needed(const HamView &H, int n_pt, int n_sh, int L) {
+template <typename R>
+size_t MultiShift<R>::bytes_needed(const HamView &H, int n_pt, int n_sh, int L) {
   const int64_t n = (int64_t)n_pt * n_sh;
-  int64_t b = align256(2 * n * H.n * L * (int64_t)sizeof(double2));          // P
+  int64_t b = align256(2 * n * H.n * L * (int64_t)sizeof(C));                 // P
   b += 4 * align256(n * L * (int64_t)sizeof(double2)) + align256((int64_t)n_pt * L * sizeof(double2));
   b += align256((int64_t)n_sh * sizeof(double)) + 3 * align256(n * L * (int64_t)sizeof(int)) + 512;
-  return (size_t)b + Bicg<double>::bytes_needed(H, n_pt, L) +
-         (size_t)align256(2 * n * H.n * L * (int64_t)sizeof(double2));         // X
+  return (size_t)b + Bicg<R>::bytes_needed(H, n_pt, L) +
+         (size_t)align256(2 * n * H.n * L * (int64_t)sizeof(C));                // X
 }
 
-cbs_status MultiShift::alloc(const HamView &H, int n_pt_, int n_sh_, int L_) {
+template <typename R>
+cbs_status MultiShift<R>::alloc(const HamView &H, int n_pt_, int n_sh_, int L_) {
   n_pt = n_pt_; n_sh = n_sh_; L = L_; N = H.n;
   CBS_TRY_B(seed.alloc(H, n_pt, L));
   const int64_t n = (int64_t)n_pt * n_sh;
-  const int64_t vec = align256(2 * n * N * L * (int64_t)sizeof(double2));
-  const int64_t bytes = (int64_t)bytes_needed(H, n_pt, n_sh, L) - (int64_t)Bicg<double>::bytes_needed(H, n_pt, L) - vec;
+  const int64_t vec = align256(2 * n * N * L * (int64_t)sizeof(C));
+  const int64_t bytes = (int64_t)bytes_needed(H, n_pt, n_sh, L) - (int64_t)Bicg<R>::bytes_needed(H, n_pt, L) - vec;
   if (cudaMalloc(&block, bytes) != cudaSuccess) {
     block = nullptr;
     set_error("cudaMalloc of the shifted-family BiCG state failed (reduce energies_per_batch)");
@@ -726,10 +833,10 @@ cbs_status MultiShift::alloc(const HamView &H, int n_pt_, int n_sh_, int L_) {
     set_error("cudaMalloc of the shifted-family solutions failed (reduce energies_per_batch)");
     return CBS_ENOMEM;
   }
-  X = (double2 *)xblock;
+  X = (C *)xblock;
   char *b = (char *)block;
   auto take = [&](int64_t sz) { char *r = b; b += align256(sz); return (void *)r; };
-  P = (double2 *)take(2 * n * N * L * (int64_t)sizeof(double2));
+  P = (C *)take(2 * n * N * L * (int64_t)sizeof(C));
   pi = (double2 *)take(n * L * (int64_t)sizeof(double2));
   pi_prev = (double2 *)take(n * L * (int64_t)sizeof(double2));
   cb = (double2 *)take(n * L * (int64_t)sizeof(double2));
@@ -744,7 +851,8 @@ cbs_status MultiShift::alloc(const HamView &H, int n_pt_, int n_sh_, int L_) {
   return CBS_OK;
 }
 
-cbs_status MultiShift::update_columns(cudaStream_t st, double *out) {
+template <typename R>
+cbs_status MultiShift<R>::update_columns(cudaStream_t st, double *out) {
   unsigned long long v = 0;
   CBS_CUDA(cudaMemcpyAsync(&v, upd_cols, sizeof(v), cudaMemcpyDeviceToHost, st));
   CBS_CUDA(cudaStreamSynchronize(st));
@@ -752,7 +860,8 @@ cbs_status MultiShift::update_columns(cudaStream_t st, double *out) {
   return CBS_OK;
 }
 
-void MultiShift::release() {
+template <typename R>
+void MultiShift<R>::release() {
   seed.release();
   for (int k = 0; k < n_upd_ev; ++k) cudaEventDestroy(upd_ev[k]);
   n_upd_ev = 0;
@@ -763,13 +872,15 @@ void MultiShift::release() {
   exec_max_iter = exec_check_every = -1;
 }
 
-void MultiShift::release_x() {
+template <typename R>
+void MultiShift<R>::release_x() {
   if (xblock) cudaFree(xblock);
   xblock = nullptr;
   X = nullptr;
 }
 
-cbs_status MultiShift::init(const double2 *z1, double E0, const double *sigma_h, const double2 *B,
+template <typename R>
+cbs_status MultiShift<R>::init(const double2 *z1, double E0, const double *sigma_h, const double2 *B,
                             double tol, cudaStream_t st) {
   std::vector<double> hE(n_pt, E0);
   CBS_CUDA(cudaMemcpyAsync(seed.E, hE.data(), n_pt * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -778,26 +889,27 @@ cbs_status MultiShift::init(const double2 *z1, double E0, const double *sigma_h,
   CBS_CUDA(cudaStreamSynchronize(st));            // hE, sigma_h are host temporaries
   CBS_TRY_B(seed.init(B, 0, B, 0, nullptr, tol, 0.0, st));
   const int64_t n = (int64_t)n_pt * n_sh;
-  CBS_CUDA(cudaMemsetAsync(X, 0, 2 * n * N * L * sizeof(double2), st));
-  CBS_CUDA(cudaMemsetAsync(P, 0, 2 * n * N * L * sizeof(double2), st));
+  CBS_CUDA(cudaMemsetAsync(X, 0, 2 * n * N * L * sizeof(C), st));
+  CBS_CUDA(cudaMemsetAsync(P, 0, 2 * n * N * L * sizeof(C), st));
   k_ms_init<<<n_pt, L, 0, st>>>(n_pt, n_sh, L, seed.active, pi, pi_prev, alpha_prev, sactive, siters,
                                 sflags); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }
 
-cbs_status MultiShift::step(int max_iter, cudaStream_t st, int kk) {
-  Bicg<double> &b = seed;
+template <typename R>
+cbs_status MultiShift<R>::step(int max_iter, cudaStream_t st, int kk) {
+  Bicg<R> &b = seed;
   dim3 blk = col_block(L);
   dim3 grd((unsigned)b.n_chunks, (unsigned)n_pt, 1);
-  k_update_p<double><<<grd, blk, 0, st>>>(n_pt, N, L, b.chunk_pts, b.r, b.p, b.beta, b.active, b.sys_active); cbs::count_launches(1);
+  k_update_p<R><<<grd, blk, 0, st>>>(n_pt, N, L, b.chunk_pts, b.r, b.p, b.beta, b.active, b.sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   const bool prof = b.profile && kk >= 0 && 2 * kk + 1 < b.n_prof_ev;
   if (prof) CBS_CUDA(cudaEventRecordWithFlags(b.prof_ev[2 * kk], st, cudaEventRecordExternal));
-  cbs_status s = apply_P<double>(b.H, 2 * n_pt, L, b.p, b.q, b.tw, false, b.E, b.D, b.sys_active, st);
+  cbs_status s = bicg_apply(b, b.p, b.q, st);
   if (s != CBS_OK) return s;
   if (prof) CBS_CUDA(cudaEventRecordWithFlags(b.prof_ev[2 * kk + 1], st, cudaEventRecordExternal));
-  k_dot_pq<double><<<grd, blk, red_smem(L), st>>>(n_pt, N, L, b.chunk_pts, b.n_chunks, b.p, b.q, b.part, b.sys_active); cbs::count_launches(1);
+  k_dot_pq<R><<<grd, blk, red_smem(L), st>>>(n_pt, N, L, b.chunk_pts, b.n_chunks, b.p, b.q, b.part, b.sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   k_reduce_alpha<<<n_pt, L, 0, st>>>(n_pt, L, b.n_chunks, b.part, b.rho, b.alpha, b.active, b.flags, b.sys_active,
                                      b.sys_apply); cbs::count_launches(1);
@@ -807,10 +919,10 @@ cbs_status MultiShift::step(int max_iter, cudaStream_t st, int kk) {
   CBS_CUDA(cudaGetLastError());
   const bool uprof = b.profile && kk >= 0 && 2 * kk + 1 < n_upd_ev;
   if (uprof) CBS_CUDA(cudaEventRecordWithFlags(upd_ev[2 * kk], st, cudaEventRecordExternal));
-  k_ms_update<<<grd, blk, 0, st>>>(n_pt, n_sh, N, L, b.chunk_pts, b.r, P, X, cb, ca, sactive, b.sys_active); cbs::count_launches(1);
+  k_ms_update<R><<<grd, blk, 0, st>>>(n_pt, n_sh, N, L, b.chunk_pts, b.r, P, X, cb, ca, sactive, b.sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   if (uprof) CBS_CUDA(cudaEventRecordWithFlags(upd_ev[2 * kk + 1], st, cudaEventRecordExternal));
-  k_pass_b<double><<<grd, blk, red_smem(L), st>>>(n_pt, N, L, b.chunk_pts, b.n_chunks, nullptr, b.r, b.p, b.q,
+  k_pass_b<R><<<grd, blk, red_smem(L), st>>>(n_pt, N, L, b.chunk_pts, b.n_chunks, nullptr, b.r, b.p, b.q,
                                                   b.alpha, b.active, b.part, b.sys_active); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   CBS_CUDA(cudaMemsetAsync(b.n_active, 0, sizeof(int), st));
@@ -818,11 +930,18 @@ cbs_status MultiShift::step(int max_iter, cudaStream_t st, int kk) {
                                        b.active, b.iters, b.flags, max_iter, b.sys_active, b.n_active, pi,
                                        sactive, siters, sflags); cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
+  if (group_need < n_pt) {
+    k_ms_group_stop<<<n_sh, ((n_pt + 31) / 32) * 32, 0, st>>>(n_pt, L, group_need, sactive, sflags, siters,
+                                                                b.iters);
+    cbs::count_launches(1);
+    CBS_CUDA(cudaGetLastError());
+  }
   return CBS_OK;
 }
 
-cbs_status MultiShift::iterate(int max_iter, int check_every, cudaStream_t st, int *host_iters_done) {
-  Bicg<double> &b = seed;
+template <typename R>
+cbs_status MultiShift<R>::iterate(int max_iter, int check_every, cudaStream_t st, int *host_iters_done) {
+  Bicg<R> &b = seed;
   if (check_every < 1) check_every = 1;
   if (b.profile && b.n_prof_ev == 0) {
     const int ne = 2 * (check_every < 64 ? check_every : 64);
@@ -883,6 +1002,9 @@ cbs_status MultiShift::iterate(int max_iter, int check_every, cudaStream_t st, i
   if (host_iters_done) *host_iters_done = done;
   return s;
 }
+
+template struct MultiShift<double>;
+template struct MultiShift<float>;
 
 // ---------------------------------------------------------------- refinement helpers
 // AY holds P(z)Y (primal, systems 0..n-1) and P(z)^dagger Y~ (dual, n..2n-1); replace by

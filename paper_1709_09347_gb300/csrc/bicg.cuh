@@ -40,8 +40,17 @@ struct Bicg {
   int exec_max_iter = -1, exec_check_every = -1;
   uint64_t exec_kernels = 0;
   int *h_active = nullptr;                   // pinned host word for the convergence poll
+  // load-balance rule (§3.3): systems come in groups of `group` quadrature points of one
+  // energy (0 = no groups); a group's remaining systems stop once more than group_need of
+  // them have stopped
+  int group = 0, group_need = 0;
+  // FP64 vectors and recurrences with the operator applied in complex64 (set before alloc;
+  // R = double only): q = P(z) p is formed from p rounded to complex64, with FP32
+  // accumulation, and widened back
+  bool apply32 = false;
+  float2 *p32 = nullptr, *q32 = nullptr, *D32 = nullptr;
 
-  static size_t bytes_needed(const HamView &H, int n, int L);
+  static size_t bytes_needed(const HamView &H, int n, int L, bool apply32 = false);
   cbs_status alloc(const HamView &H, int n, int L);
   void release();
   // Set twists/energies: primal twist z[s], dual twist 1/conj(z[s]); z, E on device.
@@ -80,12 +89,18 @@ struct Bicg {
 // Energy e of point j stops when ||r|| / |pi_e| and ||r~|| / |pi_e| are below tol ||b||;
 // the seed runs while any of its energies is active.  Outputs X [2n][N][L] with
 // n = n_sh * n_pt systems ordered e * n_pt + j (primal), then their duals.
+// R = double: the whole family in FP64.  R = float: the seed recursion, the scaled
+// directions and the solutions in complex64 (the scalar recurrences for pi, alpha, beta
+// stay in FP64); its solutions are accurate to the single-precision level and are refined
+// per energy afterwards.
+template <typename R>
 struct MultiShift {
-  Bicg<double> seed;                      // n_pt seed systems (and duals) at energy E_0
+  typedef typename CT<R>::T C;
+  Bicg<R> seed;                           // n_pt seed systems (and duals) at energy E_0
   int n_pt = 0, n_sh = 0, L = 0;
   int64_t N = 0;
-  double2 *X = nullptr;                   // [2n][N][L] solutions (separate allocation)
-  double2 *P = nullptr;                   // [2n][N][L] scaled search directions pi_e p_e
+  C *X = nullptr;                         // [2n][N][L] solutions (separate allocation)
+  C *P = nullptr;                         // [2n][N][L] scaled search directions pi_e p_e
   double2 *pi = nullptr, *pi_prev = nullptr;            // [n][L]
   double2 *cb = nullptr, *ca = nullptr;  // [n][L] this iteration's coefficients
   double2 *alpha_prev = nullptr;          // [n_pt][L]
@@ -101,6 +116,9 @@ struct MultiShift {
   int n_upd_ev = 0;
   double upd_ms = 0, upd_launches = 0;
   unsigned long long *upd_cols = nullptr;
+  // load-balance rule (§3.3): an energy's remaining points stop once more than group_need
+  // of its n_pt points have converged (group_need >= n_pt: off)
+  int group_need = 1 << 30;
 
   static size_t bytes_needed(const HamView &H, int n_pt, int n_sh, int L);
   cbs_status update_columns(cudaStream_t st, double *out);

@@ -162,6 +162,10 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
                         typename CT<R>::T *Y, const double2 *twist, bool per_col,
                         const double *E, const typename CT<R>::T *D, const int *sys_active,
                         cudaStream_t st);
+// Whether the operator apply supports L columns of element type dtype on this cell:
+// complex128 up to 256 columns; complex64 up to 256, or up to 512 with an even L and at
+// most 4 projectors (two columns per thread).  Sets the error message when it does not.
+bool apply_supported(const HamView &H, int L, int dtype, const char *who);
 // Y = P(w) X for n_sys systems; D is scratch of n_sys*n_atoms*np4*L elements
 template <typename R>
 cbs_status apply_P(const HamView &H, int n_sys, int L, const typename CT<R>::T *X,

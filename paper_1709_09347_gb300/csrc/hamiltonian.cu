@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -194,6 +195,35 @@ extern "C" cbs_status cbs_hamiltonian_norms(const cbs_hamiltonian *h, double E, 
   return CBS_OK;
 }
 
+// Exact Frobenius norms of H+, H- and the pieces of ||H0 - E||_F, on the device.
+static cbs_status compute_norms(cbs_hamiltonian *h) {
+  HamView &v = h->v;
+  // exact Frobenius norms on the device
+  const int threads = 128;
+  const int nb = ceil_div(v.n, threads);
+  double *part = nullptr, *out = nullptr;
+  int *err = nullptr;
+  CBS_CUDA(cudaMalloc(&part, (size_t)nb * 5 * sizeof(double)));
+  CBS_CUDA(cudaMalloc(&out, 5 * sizeof(double) + sizeof(int)));
+  err = (int *)(out + 5);
+  CBS_CUDA(cudaMemset(err, 0, sizeof(int)));
+  k_frobenius<<<nb, threads>>>(v, part, err); cbs::count_launches(1);
+  k_sum_parts<<<1, 32>>>(part, nb, out); cbs::count_launches(1);
+  double res[5];
+  int herr = 0;
+  cudaError_t e1 = cudaMemcpy(res, out, sizeof(res), cudaMemcpyDeviceToHost);
+  cudaError_t e2 = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(part);
+  cudaFree(out);
+  if (e1 != cudaSuccess) return cuda_fail(e1, "Frobenius norm kernel");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "Frobenius norm kernel");
+  if (herr == 1) { set_error("more than 64 atoms cover one grid point"); return CBS_EINVAL; }
+  if (herr == 2) { set_error("projector coupling beyond the neighbouring cells"); return CBS_EINVAL; }
+  h->fro_off0 = res[0]; h->fro_p2 = res[1]; h->fro_m2 = res[2];
+  h->diag_sum = res[3]; h->diag_sum2 = res[4];
+  return CBS_OK;
+}
+
 static cbs_status create_impl(const cbs_grid *g, const double *v_loc, const cbs_projectors *P,
                               cbs_hamiltonian *h) {
   HamView &v = h->v;
@@ -320,30 +350,7 @@ static cbs_status create_impl(const cbs_grid *g, const double *v_loc, const cbs_
     if ((s = upload(h, pt_ptr.data(), N + 1, &v.pt_ptr)) != CBS_OK) return s;
   }
 
-  // exact Frobenius norms on the device
-  const int threads = 128;
-  const int nb = ceil_div(v.n, threads);
-  double *part = nullptr, *out = nullptr;
-  int *err = nullptr;
-  CBS_CUDA(cudaMalloc(&part, (size_t)nb * 5 * sizeof(double)));
-  CBS_CUDA(cudaMalloc(&out, 5 * sizeof(double) + sizeof(int)));
-  err = (int *)(out + 5);
-  CBS_CUDA(cudaMemset(err, 0, sizeof(int)));
-  k_frobenius<<<nb, threads>>>(v, part, err); cbs::count_launches(1);
-  k_sum_parts<<<1, 32>>>(part, nb, out); cbs::count_launches(1);
-  double res[5];
-  int herr = 0;
-  cudaError_t e1 = cudaMemcpy(res, out, sizeof(res), cudaMemcpyDeviceToHost);
-  cudaError_t e2 = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
-  cudaFree(part);
-  cudaFree(out);
-  if (e1 != cudaSuccess) return cuda_fail(e1, "Frobenius norm kernel");
-  if (e2 != cudaSuccess) return cuda_fail(e2, "Frobenius norm kernel");
-  if (herr == 1) { set_error("more than 64 atoms cover one grid point"); return CBS_EINVAL; }
-  if (herr == 2) { set_error("projector coupling beyond the neighbouring cells"); return CBS_EINVAL; }
-  h->fro_off0 = res[0]; h->fro_p2 = res[1]; h->fro_m2 = res[2];
-  h->diag_sum = res[3]; h->diag_sum2 = res[4];
-  return CBS_OK;
+  return compute_norms(h);
 }
 
 extern "C" cbs_status cbs_create_hamiltonian(const cbs_grid *grid, const double *v_loc,
@@ -356,4 +363,55 @@ extern "C" cbs_status cbs_create_hamiltonian(const cbs_grid *grid, const double 
   if (s != CBS_OK) { cbs_hamiltonian_free(h); return s; }
   *out = h;
   return CBS_OK;
+}
+
+namespace cbs {
+// V_loc in single precision from the FP64 copy, and a flag if any value is not finite.
+__global__ void k_vloc32(int64_t n, const double *v, float *v32, int *bad) {
+  int b = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = v[i];
+    v32[i] = (float)x;
+    b |= !isfinite(x);
+  }
+  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+}  // namespace cbs
+
+extern "C" cbs_status cbs_hamiltonian_set_vloc(cbs_hamiltonian *h, const double *v_loc) {
+  if (!h || !v_loc) { set_error("cbs_hamiltonian_set_vloc: null argument"); return CBS_EINVAL; }
+  HamView &v = h->v;
+  const size_t N = (size_t)v.n;
+  int *bad = nullptr;
+  double *tmp = nullptr;
+  CBS_CUDA(cudaMalloc(&tmp, N * sizeof(double) + 256));
+  bad = (int *)((char *)tmp + ((N * sizeof(double) + 127) & ~(size_t)127));
+  cbs_status s = CBS_OK;
+  cudaError_t e = cudaMemcpy(tmp, v_loc, N * sizeof(double), cudaMemcpyDefault);
+  if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    // check into a scratch copy first, so a rejected V_loc leaves the handle unchanged
+    k_vloc32<<<std::min<int64_t>(1024, ((int64_t)N + 255) / 256), 256>>>((int64_t)N, tmp,
+                                                                         const_cast<float *>(v.vloc32), bad);
+    cbs::count_launches(1);
+    e = cudaGetLastError();
+  }
+  int hb = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) s = cuda_fail(e, "cbs_hamiltonian_set_vloc");
+  else if (hb) {
+    // restore the single-precision copy from the unchanged FP64 one
+    k_vloc32<<<std::min<int64_t>(1024, ((int64_t)N + 255) / 256), 256>>>((int64_t)N, v.vloc,
+                                                                         const_cast<float *>(v.vloc32), bad);
+    cbs::count_launches(1);
+    cudaDeviceSynchronize();
+    set_error("v_loc contains a non-finite value");
+    s = CBS_EINVAL;
+  } else {
+    e = cudaMemcpy(const_cast<double *>(v.vloc), tmp, N * sizeof(double), cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) s = cuda_fail(e, "cbs_hamiltonian_set_vloc copy");
+  }
+  cudaFree(tmp);
+  if (s != CBS_OK) return s;
+  return compute_norms(h);
 }

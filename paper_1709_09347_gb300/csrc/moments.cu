@@ -39,24 +39,27 @@ cbs_status launch_contour(int n_int, int M, double lambda_min, double2 *coef, do
   return CBS_OK;
 }
 
-// S[e][i][k][c] for k < M from the n_int primal (system e*n_int + j) and dual
-// (n + e*n_int + j) solutions stored in Y[2n][N][L].
+// S[e][i][k][c] for k < M from the n_w primal (system e*n_w + jj) and dual (n + e*n_w + jj)
+// solutions stored in Y[2n][N][L], n = n_e * n_w, of quadrature points j = j0 + jj; with
+// `accumulate` the wave's sum is added to S (points streamed in waves), else it replaces S.
 template <int MM>
-__global__ void k_moments(int n, int n_int, int M, int64_t N, int L, const double2 *__restrict__ Y,
-                          const double2 *__restrict__ coef, double2 *__restrict__ S) {
+__global__ void k_moments(int n, int n_w, int j0, int M, int64_t N, int L, const double2 *__restrict__ Y,
+                          const double2 *__restrict__ coef, double2 *__restrict__ S, int accumulate) {
   const int e = blockIdx.y, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
   const int M2 = 2 * M;
   const int64_t per = (int64_t)py * 4;
   const int64_t i0 = (int64_t)blockIdx.x * per;
   for (int64_t i = i0 + ly; i < min(N, i0 + per); i += py) {
     double2 acc[MM];
+    double2 *Se = S + ((int64_t)e * N + i) * M * L;
 #pragma unroll
-    for (int k = 0; k < MM; ++k) acc[k] = make_double2(0, 0);
-    for (int j = 0; j < n_int; ++j) {
-      const int64_t s = (int64_t)e * n_int + j;
+    for (int k = 0; k < MM; ++k)
+      acc[k] = (accumulate && k < M) ? Se[(int64_t)k * L + c] : make_double2(0, 0);
+    for (int jj = 0; jj < n_w; ++jj) {
+      const int64_t s = (int64_t)e * n_w + jj;
       const double2 y1 = Y[(s * N + i) * L + c];
       const double2 y2 = Y[((n + s) * N + i) * L + c];
-      const double2 *a = coef + (int64_t)j * 2 * M2;
+      const double2 *a = coef + (int64_t)(j0 + jj) * 2 * M2;
       const double2 *b = a + M2;
 #pragma unroll
       for (int k = 0; k < MM; ++k)
@@ -65,21 +68,20 @@ __global__ void k_moments(int n, int n_int, int M, int64_t N, int L, const doubl
           acc[k] = cfma(make_double2(-b[k].x, -b[k].y), y2, acc[k]);
         }
     }
-    double2 *Se = S + ((int64_t)e * N + i) * M * L;
 #pragma unroll
     for (int k = 0; k < MM; ++k)
       if (k < M) Se[(int64_t)k * L + c] = acc[k];
   }
 }
 
-cbs_status launch_moments(int n, int n_e, int n_int, int M, int64_t N, int L, const double2 *Y,
-                          const double2 *coef, double2 *S, cudaStream_t st) {
+cbs_status launch_moments(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, const double2 *Y,
+                          const double2 *coef, double2 *S, bool accumulate, cudaStream_t st) {
   dim3 blk = col_block(L);
   dim3 grd((unsigned)ceil_div(N, (int64_t)blk.y * 4), (unsigned)n_e, 1);
   if (M <= 8)
-    k_moments<8><<<grd, blk, 0, st>>>(n, n_int, M, N, L, Y, coef, S);
+    k_moments<8><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, accumulate ? 1 : 0);
   else if (M <= 16)
-    k_moments<16><<<grd, blk, 0, st>>>(n, n_int, M, N, L, Y, coef, S);
+    k_moments<16><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, accumulate ? 1 : 0);
   else {
     set_error("M must be <= 16");
     return CBS_EINVAL;
@@ -130,26 +132,28 @@ __global__ void k_vhy(int64_t N, int L, int n_chunks, const double2 *__restrict_
   }
 }
 
-// mu[e][k][c1][c2] = sum_j sum_chunks a_jk G_j - b_jk G~_j
-__global__ void k_mu(int n, int n_int, int M2, int L, int n_chunks, const double2 *part,
-                     const double2 *coef, double2 *mu) {
+// mu[e][k][c1][c2] (+)= sum_jj sum_chunks a_{j0+jj,k} G_jj - b_{j0+jj,k} G~_jj over the wave's
+// points
+__global__ void k_mu(int n, int n_w, int j0, int M2, int L, int n_chunks, const double2 *part,
+                     const double2 *coef, double2 *mu, int accumulate) {
   const int e = blockIdx.y, k = blockIdx.x;
   const int LL = L * L;
   for (int pidx = threadIdx.x; pidx < LL; pidx += blockDim.x) {
-    double2 acc = make_double2(0, 0);
-    for (int j = 0; j < n_int; ++j) {
-      const int64_t s = (int64_t)e * n_int + j;
+    double2 *out = mu + (((int64_t)e * M2) + k) * LL + pidx;
+    double2 acc = accumulate ? *out : make_double2(0, 0);
+    for (int jj = 0; jj < n_w; ++jj) {
+      const int64_t s = (int64_t)e * n_w + jj;
       double2 g = make_double2(0, 0), gd = make_double2(0, 0);
       for (int ch = 0; ch < n_chunks; ++ch) {
         g = cadd(g, part[(s * n_chunks + ch) * LL + pidx]);
         gd = cadd(gd, part[((n + s) * n_chunks + ch) * LL + pidx]);
       }
-      const double2 a = coef[((int64_t)j * 2 + 0) * M2 + k];
-      const double2 b = coef[((int64_t)j * 2 + 1) * M2 + k];
+      const double2 a = coef[((int64_t)(j0 + jj) * 2 + 0) * M2 + k];
+      const double2 b = coef[((int64_t)(j0 + jj) * 2 + 1) * M2 + k];
       acc = cfma(a, g, acc);
       acc = cfma(make_double2(-b.x, -b.y), gd, acc);
     }
-    mu[(((int64_t)e * M2) + k) * LL + pidx] = acc;
+    *out = acc;
   }
 }
 
@@ -160,9 +164,9 @@ int vhy_chunks(int64_t N) {
   return (int)c;
 }
 
-cbs_status launch_mu(int n, int n_e, int n_int, int M, int64_t N, int L, const double2 *V,
+cbs_status launch_mu(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, const double2 *V,
                      const double2 *Y, const double2 *coef, double2 *part, double2 *mu,
-                     cudaStream_t st) {
+                     bool accumulate, cudaStream_t st) {
   if (L > 64) {
     set_error("L must be <= 64 for the moment kernel");
     return CBS_EINVAL;
@@ -175,8 +179,9 @@ cbs_status launch_mu(int n, int n_e, int n_int, int M, int64_t N, int L, const d
   else k_vhy<16><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
   cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
-  k_mu<<<dim3((unsigned)(2 * M), (unsigned)n_e, 1), 256, 0, st>>>(n, n_int, 2 * M, L, nch, part,
-                                                                 coef, mu); cbs::count_launches(1);
+  k_mu<<<dim3((unsigned)(2 * M), (unsigned)n_e, 1), 256, 0, st>>>(n, n_w, j0, 2 * M, L, nch, part,
+                                                                 coef, mu, accumulate ? 1 : 0);
+  cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;
 }

@@ -16,7 +16,10 @@ constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Host code cannot use g_noalloc_scratch as a device address (its name is a host-side
-// stand-in), so the address is looked up once per device, with that device current.
+// stand-in), so the address is looked up once per device, with that device current.  With
+// CUDA's lazy module loading (the default) that first lookup is also what loads this
+// library's device code on the device and reserves the array there.  The cached address
+// belongs to the device's primary context: it is stale after a device reset.
 constexpr int kMaxDevices = 64;
 static void *g_scratch_addr[kMaxDevices] = {};
 static std::mutex g_scratch_mu;
@@ -48,11 +51,13 @@ using namespace cbs;
 extern "C" cbs_status cbs_apply_noalloc(const cbs_hamiltonian *h, int n_sys, const double *z,
                                         const double *E, int L, const void *X, void *Y, int dtype,
                                         void *stream) {
-  if (!h || !z || !E || !X || !Y || n_sys < 1 || L < 1 || L > 1024) {
-    set_error("cbs_apply_noalloc: bad argument (need n_sys >= 1, 1 <= L <= 1024, non-null pointers)");
+  if (!h || !z || !E || !X || !Y || n_sys < 1 || L < 1 || L > 512) {
+    set_error("cbs_apply_noalloc: bad argument (need n_sys >= 1, 1 <= L <= 512, non-null pointers)");
     return CBS_EINVAL;
   }
   if (dtype != CBS_C128 && dtype != CBS_C64) { set_error("cbs_apply_noalloc: dtype"); return CBS_EINVAL; }
+  // the same column limits as cbs_apply, checked before anything is queued on the stream
+  if (!apply_supported(h->v, L, dtype, "cbs_apply_noalloc")) return CBS_EINVAL;
   const size_t tw_bytes = round256((size_t)n_sys * sizeof(double2));
   const size_t e_bytes = round256((size_t)n_sys * sizeof(double));
   const size_t d_bytes = cbs_apply_workspace_size(h, n_sys, L, dtype);

@@ -83,6 +83,34 @@ __global__ void k_expand_systems(int n_e, int n_int, const double2 *z1, const do
   }
 }
 
+// Sets *bad when any of the count complex entries of A is not finite.
+__global__ void k_nonfinite(int64_t count, const double2 *A, int *bad) {
+  int b = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b |= !(isfinite(A[i].x) && isfinite(A[i].y));
+  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
+// Host-side check of a right-hand-side block on the device: CBS_EINVAL with a message
+// when it holds a NaN or an infinity (BiCG on such a block would only spread it).
+static cbs_status check_finite_block(int64_t count, const double2 *A, const char *who, cudaStream_t st) {
+  DevBuf flag;
+  CBS_TRY(flag.alloc(sizeof(int)));
+  CBS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+  k_nonfinite<<<std::min<int64_t>(1024, (count + 255) / 256), 256, 0, st>>>(count, A, flag.as<int>());
+  cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  int bad = 0;
+  CBS_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CBS_CUDA(cudaStreamSynchronize(st));
+  if (bad) {
+    set_error(std::string(who) + ": the right-hand sides contain a NaN or an infinity");
+    return CBS_EINVAL;
+  }
+  return CBS_OK;
+}
+
 __global__ void k_col_norms(int64_t N, int L, const double2 *B, double *out) {
   const int c = threadIdx.x;
   double a = 0;
@@ -184,6 +212,9 @@ struct ResidualCheck {
 struct ShiftedSolver {
   HamView H;
   int n = 0, L = 0;
+  const double2 *zs = nullptr;   // [n] twists of the primal systems (device)
+  const double *Es = nullptr;    // [n] energies (device)
+  const double2 *B = nullptr;    // [N][L] right-hand sides shared by every system (device)
   DevBuf ybuf;
   double2 *Y = nullptr;      // [2n][N][L] solutions (FP64)
   Bicg<double> b64;
@@ -193,87 +224,215 @@ struct ShiftedSolver {
   std::vector<double> maxrel;
   int sweeps = 0;
   bool fp64_continued = false;
+  // quadrature points per energy when the systems are energies x points (e-major), for the
+  // load-balance rule (0: systems are independent)
+  int group = 0;
   double prof_ms[3] = {0, 0, 0}, prof_launches[3] = {0, 0, 0}, prof_outputs[3] = {0, 0, 0};
+  // columns that the load-balance rule stopped (flag bit 6) are not refined: clear them in
+  // the residual check's mask and recount the columns left
+  cbs_status mask_stopped(int *unconv, cudaStream_t st) {
+    bool any = false;
+    for (int f : flags) any = any || (f & 64);
+    if (!any || *unconv == 0) return CBS_OK;
+    std::vector<int> m((size_t)n * L);
+    CBS_CUDA(cudaMemcpyAsync(m.data(), rc.colmask, m.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaStreamSynchronize(st));
+    int u = 0;
+    for (size_t k = 0; k < m.size(); ++k) {
+      if (flags[k] & 64) m[k] = 0;
+      u += m[k];
+    }
+    CBS_CUDA(cudaMemcpyAsync(rc.colmask, m.data(), m.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CBS_CUDA(cudaStreamSynchronize(st));
+    *unconv = u;
+    return CBS_OK;
+  }
+  static int stop_need(const cbs_options &o, int n_pt) {
+    return o.stop_fraction < 1.0 ? (int)floor(o.stop_fraction * n_pt) : (1 << 30);
+  }
+  // adds the apply profiles of b64, b32 and the residual checks (and resets them)
   cbs_status collect_profile(cudaStream_t st) {
     double o64 = 0, o32 = 0;
     if (b64.block && b64.profile) CBS_TRY(b64.prof_outputs(st, &o64));
-    if (b32.block && b32.profile) {
-      CBS_TRY(b32.prof_outputs(st, &o32));
-      prof32_ms = b32.prof_ms;
-      prof32_launches = b32.prof_launches;
-      prof32_outputs = o32;
-    }
-    prof_ms[CBS_C128] = b64.prof_ms + rc.prof_ms;
-    prof_launches[CBS_C128] = b64.prof_launches + rc.prof_launches;
-    prof_outputs[CBS_C128] = o64 + rc.prof_outputs;
-    prof_ms[CBS_C64] = prof32_ms;
-    prof_launches[CBS_C64] = prof32_launches;
-    prof_outputs[CBS_C64] = prof32_outputs;
+    if (b32.block && b32.profile) CBS_TRY(b32.prof_outputs(st, &o32));
+    prof_ms[CBS_C128] += b64.prof_ms + rc.prof_ms;
+    prof_launches[CBS_C128] += b64.prof_launches + rc.prof_launches;
+    prof_outputs[CBS_C128] += o64 + rc.prof_outputs;
+    prof_ms[CBS_C64] += b32.prof_ms;
+    prof_launches[CBS_C64] += b32.prof_launches;
+    prof_outputs[CBS_C64] += o32;
+    b64.prof_ms = b64.prof_launches = b32.prof_ms = b32.prof_launches = 0;
+    rc.prof_ms = rc.prof_launches = rc.prof_outputs = 0;
+    if (b64.block && b64.sys_apply) CBS_CUDA(cudaMemsetAsync(b64.sys_apply, 0, sizeof(unsigned long long), st));
+    if (b32.block && b32.sys_apply) CBS_CUDA(cudaMemsetAsync(b32.sys_apply, 0, sizeof(unsigned long long), st));
     return CBS_OK;
   }
-  double prof32_ms = 0, prof32_launches = 0, prof32_outputs = 0;
 
+  // device bytes of the per-system solver state (one BiCG per system), per primal system
   static size_t bytes_per_system(const HamView &H, int L, int precision) {
     const size_t v16 = (size_t)H.n * L * 16;
     if (precision == CBS_FP64) return 2 * (4 * v16 + v16) + 2 * v16;   // state + residual check
+    if (precision == CBS_FP64_APPLY32) return 2 * (4 * v16 + v16) + 2 * v16 + 2 * v16;   // + complex64 p, q
     return 2 * (4 * v16 / 2) + 2 * v16 + 2 * v16 + 2 * v16;             // f32 state, Y, R, D
   }
+  // device bytes per energy of a shifted family of n_pt points: scaled directions and
+  // solutions of its 2 n_pt systems, plus the FP64 solutions kept for the moments
+  static size_t family_bytes_per_energy(const HamView &H, int n_pt, int L, int precision) {
+    const size_t v16 = (size_t)H.n * L * 16;
+    const bool fp64 = precision != CBS_FP32_REFINE;
+    const size_t vr = fp64 ? v16 : v16 / 2;
+    return (size_t)2 * n_pt * (2 * vr + (fp64 ? 0 : v16));
+  }
 
-  MultiShift ms;
+  MultiShift<double> ms;
+  MultiShift<float> ms32;
   DevBuf twbuf;
   ~ShiftedSolver() {
     b64.release();
     b32.release();
     ms.release();
     ms.release_x();
+    ms32.release();
+    ms32.release_x();
   }
 
-  // FP64 with one Krylov sequence per (point, column) for all n_e energies of the batch
-  // (systems ordered e * n_pt + j as in zs/Es); seed energy: the highest of the batch.
-  cbs_status run_family(const HamView &H_, int n_e, int n_pt, int L_, const double2 *z1,
-                        const double *energies_h, const double2 *zs, const double *Es,
-                        const double2 *B, const cbs_options &o, cudaStream_t st) {
-    H = H_; n = n_e * n_pt; L = L_;
+  cbs_status init_stats(int n_, int L_) {
+    n = n_; L = L_;
     iters.assign((size_t)n * L, 0);
     flags.assign((size_t)n * L, 0);
     maxrel.assign((size_t)n * L, 0.0);
+    return CBS_OK;
+  }
+
+  // Per-system BiCG from Y = 0: plain FP64, or complex64 with FP64 reliable updates.
+  cbs_status run(const HamView &H_, int n_, int L_, const double2 *zs_, const double *Es_,
+                 const double2 *B_, const cbs_options &o, cudaStream_t st) {
+    H = H_; zs = zs_; Es = Es_; B = B_;
+    init_stats(n_, L_);
     CBS_TRY(rc.alloc(H, n, L));
     rc.profile = o.profile != 0;
-    ms.seed.profile = b64.profile = o.profile != 0;
-    double E0 = energies_h[0];
-    for (int e = 1; e < n_e; ++e) E0 = std::max(E0, energies_h[e]);
-    std::vector<double> sig(n_e);
-    for (int e = 0; e < n_e; ++e) sig[e] = energies_h[e] - E0;
-    CBS_TRY(ms.alloc(H, n_pt, n_e, L));
-    CBS_TRY(ms.init(z1, E0, sig.data(), B, o.tol, st));
-    int done = 0;
-    CBS_TRY(ms.iterate(o.max_iter, o.check_every, st, &done));
-    Y = ms.X;
-    // twists and energies of every system for the true-residual check
+    b64.profile = b32.profile = o.profile != 0;
+    if (o.precision != CBS_FP32_REFINE) {
+      b64.apply32 = o.precision == CBS_FP64_APPLY32;
+      CBS_TRY(b64.alloc(H, n, L));
+      if (group > 0 && o.stop_fraction < 1.0) {
+        b64.group = group;
+        b64.group_need = stop_need(o, group);
+      }
+      CBS_TRY(b64.set_systems(zs, Es, st));
+      CBS_TRY(b64.init(B, 0, B, 0, nullptr, o.tol, 0.0, st));
+      int done = 0;
+      CBS_TRY(b64.iterate(o.tol, o.max_iter, o.check_every, st, &done));
+      if (o.precision == CBS_FP64_APPLY32) {
+        // the recursion ran on a complex64 operator: keep its solution and continue the
+        // columns whose FP64 true residual misses tol
+        CBS_TRY(ybuf.alloc((size_t)2 * n * H.n * L * sizeof(double2)));
+        Y = ybuf.as<double2>();
+        CBS_CUDA(cudaMemcpyAsync(Y, b64.x, (size_t)2 * n * H.n * L * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        CBS_CUDA(cudaMemcpyAsync(iters.data(), b64.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaMemcpyAsync(flags.data(), b64.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaStreamSynchronize(st));
+        for (auto &f : flags) f &= 2 | 64;
+        CBS_TRY(collect_profile(st));
+        b64.release();
+        return refine(o, st);
+      }
+      Y = b64.x;
+      CBS_TRY(rc.run(H, Y, B, b64.tw, b64.E, o.tol, st, nullptr));
+      CBS_CUDA(cudaMemcpyAsync(iters.data(), b64.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(flags.data(), b64.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(maxrel.data(), rc.maxrel, (size_t)n * L * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaStreamSynchronize(st));
+      sweeps = 0;
+      return collect_profile(st);
+    }
+    CBS_TRY(ybuf.alloc((size_t)2 * n * H.n * L * sizeof(double2)));
+    Y = ybuf.as<double2>();
+    CBS_CUDA(cudaMemsetAsync(Y, 0, (size_t)2 * n * H.n * L * sizeof(double2), st));
+    return refine(o, st);
+  }
+
+  // Continues the solutions Y (already holding a starting guess) until the true residual
+  // of every column is below tol: complex64 BiCG with FP64 reliable updates (precision
+  // CBS_FP32_REFINE) or FP64 BiCG on the residual equation, for the columns that need it.
+  cbs_status refine(const cbs_options &o, cudaStream_t st) {
+    if (!rc.R) {
+      CBS_TRY(rc.alloc(H, n, L));
+      rc.profile = o.profile != 0;
+    }
+    b64.profile = b32.profile = o.profile != 0;
+    std::vector<int> it_tmp((size_t)n * L), fl_tmp((size_t)n * L);
     CBS_TRY(twbuf.alloc((size_t)2 * n * (sizeof(double2) + sizeof(double)) + 256));
     double2 *tw = twbuf.as<double2>();
     double *E2 = (double *)(tw + 2 * n);
     CBS_TRY(launch_twists(n, zs, Es, tw, E2, st));
     int unconv = 0;
     CBS_TRY(rc.run(H, Y, B, tw, E2, o.tol, st, &unconv));
-    std::vector<int> it_tmp((size_t)n * L), fl_tmp((size_t)n * L);
-    CBS_CUDA(cudaMemcpyAsync(iters.data(), ms.siters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), ms.sflags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CBS_CUDA(cudaStreamSynchronize(st));
-    for (size_t k = 0; k < flags.size(); ++k) flags[k] |= (fl_tmp[k] & 2);
-    double oseed = 0;
-    if (o.profile) CBS_TRY(ms.seed.prof_outputs(st, &oseed));
-    const double seed_ms = ms.seed.prof_ms, seed_launches = ms.seed.prof_launches;
-    double upd_cols = 0;
-    if (o.profile) CBS_TRY(ms.update_columns(st, &upd_cols));
-    const double upd_ms = ms.upd_ms, upd_launches = ms.upd_launches;
-    ms.release();   // keeps X (= Y)
+    CBS_TRY(mask_stopped(&unconv, st));
+    if (unconv > 0 && o.precision == CBS_FP32_REFINE) {
+      // complex64 BiCG with FP64 refinement of the residual (reliable updates):
+      //   the complex64 recursion runs until its residual is below inner_tol times the
+      //   largest residual norm seen since the last update (or inner_max_iter iterations);
+      //   its correction is added to Y in FP64, the true residuals R = B - P(z) Y and
+      //   R~ = B - P(z)^dagger Y~ are formed in FP64, and the columns above tol continue
+      //   from R (rounded) with their search directions kept.  Stop targets are relative
+      //   to the original right-hand side.
+      CBS_TRY(b32.alloc(H, n, L));
+      CBS_TRY(b32.set_systems(zs, Es, st));
+      CBS_TRY(b32.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
+                       rc.colmask, 0.25 * o.tol, o.inner_tol, st, rc.bn2));
+      std::vector<double> rel((size_t)n * L), best((size_t)n * L, 1e300);
+      std::vector<int> need((size_t)n * L), stall((size_t)n * L, 0);
+      for (int sw = 0; sw < o.max_sweeps && unconv > 0; ++sw) {
+        int done = 0;
+        CBS_TRY(b32.iterate(o.tol, o.max_iter, o.check_every, st, &done, o.inner_max_iter));
+        CBS_TRY(launch_accumulate((int64_t)2 * n * H.n * L, Y, b32.x, st));
+        CBS_TRY(rc.run(H, Y, B, tw, E2, o.tol, st, &unconv));
+        ++sweeps;
+        if (unconv == 0) break;
+        // per column: stagnation of the FP64 true residual means the single-precision
+        // recursion no longer makes progress there (loss of bi-orthogonality); such columns
+        // leave the complex64 phases and are finished in FP64 below
+        CBS_CUDA(cudaMemcpyAsync(rel.data(), rc.maxrel, rel.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaMemcpyAsync(need.data(), rc.colmask, need.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CBS_CUDA(cudaStreamSynchronize(st));
+        int live = 0;
+        for (size_t k = 0; k < rel.size(); ++k) {
+          if (!need[k]) continue;
+          if (rel[k] < 0.5 * best[k]) { best[k] = rel[k]; stall[k] = 0; }
+          else ++stall[k];
+          if (stall[k] >= o.stall_sweeps) need[k] = 0;
+          live += need[k];
+        }
+        if (live == 0) break;
+        CBS_CUDA(cudaMemcpyAsync(rc.colmask, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CBS_TRY(b32.replace(rc.R, rc.colmask, st));
+      }
+      CBS_CUDA(cudaMemcpyAsync(it_tmp.data(), b32.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), b32.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CBS_CUDA(cudaStreamSynchronize(st));
+      for (size_t k = 0; k < iters.size(); ++k) {
+        iters[k] += it_tmp[k];
+        flags[k] |= (fl_tmp[k] & 2);
+      }
+      CBS_TRY(collect_profile(st));
+      b32.release();
+      if (unconv > 0) {
+        CBS_TRY(rc.run(H, Y, B, tw, E2, o.tol, st, &unconv));   // full mask
+        CBS_TRY(mask_stopped(&unconv, st));
+      }
+    }
     if (unconv > 0) {
-      // plain FP64 BiCG on P(z) D = R, P(z)^dagger D~ = R~ for the columns left, Y += D
+      // FP64 BiCG for the columns left: P(z) D = R, P(z)^dagger D~ = R~ to tol relative to
+      // the original right-hand side, then Y += D (operator in complex64 with
+      // CBS_FP64_APPLY32: the continuation starts from a residual ~1e-6 of the original, and
+      // a complex64 apply reaches ~1e-7 of that)
+      b64.apply32 = o.precision == CBS_FP64_APPLY32;
       CBS_TRY(b64.alloc(H, n, L));
       CBS_TRY(b64.set_systems(zs, Es, st));
       CBS_TRY(b64.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
                        rc.colmask, 0.5 * o.tol, 0.0, st, rc.bn2));
+      int done = 0;
       CBS_TRY(b64.iterate(o.tol, o.max_iter, o.check_every, st, &done));
       CBS_TRY(launch_accumulate((int64_t)2 * n * H.n * L, Y, b64.x, st));
       CBS_TRY(rc.run(H, Y, B, tw, E2, o.tol, st, &unconv));
@@ -285,129 +444,112 @@ struct ShiftedSolver {
         flags[k] |= (fl_tmp[k] & 2);
       }
       fp64_continued = true;
+      CBS_TRY(collect_profile(st));
+      b64.release();
     }
     std::vector<int> mask((size_t)n * L);
     CBS_CUDA(cudaMemcpyAsync(maxrel.data(), rc.maxrel, (size_t)n * L * sizeof(double), cudaMemcpyDeviceToHost, st));
     CBS_CUDA(cudaMemcpyAsync(mask.data(), rc.colmask, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
     CBS_CUDA(cudaStreamSynchronize(st));
     for (size_t k = 0; k < mask.size(); ++k)
-      if (mask[k]) flags[k] |= 1;
-    sweeps = 0;
-    CBS_TRY(collect_profile(st));
-    prof_ms[CBS_C128] += seed_ms;
-    prof_launches[CBS_C128] += seed_launches;
-    prof_outputs[CBS_C128] += oseed;
-    prof_ms[2] = upd_ms;
-    prof_launches[2] = upd_launches;
-    prof_outputs[2] = upd_cols * (double)H.n;
+      if (mask[k] && !(flags[k] & 64)) flags[k] |= 1;
     return CBS_OK;
   }
 
-  cbs_status run(const HamView &H_, int n_, int L_, const double2 *zs, const double *Es,
-                 const double2 *B, const cbs_options &o, cudaStream_t st) {
-    H = H_; n = n_; L = L_;
-    iters.assign((size_t)n * L, 0);
-    flags.assign((size_t)n * L, 0);
-    maxrel.assign((size_t)n * L, 0.0);
-    CBS_TRY(rc.alloc(H, n, L));
-    rc.profile = o.profile != 0;
-    b64.profile = b32.profile = o.profile != 0;
-    std::vector<int> it_tmp((size_t)n * L), fl_tmp((size_t)n * L);
-    if (o.precision == CBS_FP64) {
-      CBS_TRY(b64.alloc(H, n, L));
-      CBS_TRY(b64.set_systems(zs, Es, st));
-      CBS_TRY(b64.init(B, 0, B, 0, nullptr, o.tol, 0.0, st));
-      int done = 0;
-      CBS_TRY(b64.iterate(o.tol, o.max_iter, o.check_every, st, &done));
-      Y = b64.x;
-      CBS_TRY(rc.run(H, Y, B, b64.tw, b64.E, o.tol, st, nullptr));
-      CBS_CUDA(cudaMemcpyAsync(iters.data(), b64.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaMemcpyAsync(flags.data(), b64.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaMemcpyAsync(maxrel.data(), rc.maxrel, (size_t)n * L * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaStreamSynchronize(st));
-      sweeps = 0;
-      return collect_profile(st);
-    }
-    // complex64 BiCG with FP64 refinement of the residual (reliable updates):
-    //   the complex64 recursion runs until its residual is below inner_tol times the
-    //   largest residual norm seen since the last update (or inner_max_iter iterations);
-    //   its correction is added to Y in FP64, the true residuals R = B - P(z) Y and
-    //   R~ = B - P(z)^dagger Y~ are formed in FP64, and the columns above tol continue
-    //   from R (rounded) with their search directions kept.
-    CBS_TRY(ybuf.alloc((size_t)2 * n * H.n * L * sizeof(double2)));
-    Y = ybuf.as<double2>();
-    CBS_CUDA(cudaMemsetAsync(Y, 0, (size_t)2 * n * H.n * L * sizeof(double2), st));
-    CBS_TRY(b32.alloc(H, n, L));
-    CBS_TRY(b32.set_systems(zs, Es, st));
-    sweeps = 0;
-    int unconv = 0;
-    CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));   // R = B
-    CBS_TRY(b32.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
-                     rc.colmask, 0.25 * o.tol, o.inner_tol, st));
-    std::vector<double> rel((size_t)n * L), best((size_t)n * L, 1e300);
-    std::vector<int> need((size_t)n * L), stall((size_t)n * L, 0);
-    for (int sw = 0; sw < o.max_sweeps && unconv > 0; ++sw) {
-      int done = 0;
-      CBS_TRY(b32.iterate(o.tol, o.max_iter, o.check_every, st, &done, o.inner_max_iter));
-      CBS_TRY(launch_accumulate((int64_t)2 * n * H.n * L, Y, b32.x, st));
-      CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));
-      ++sweeps;
-      if (unconv == 0) break;
-      // per column: stagnation of the FP64 true residual means the single-precision
-      // recursion no longer makes progress there (loss of bi-orthogonality); such columns
-      // leave the complex64 phases and are finished in FP64 below
-      CBS_CUDA(cudaMemcpyAsync(rel.data(), rc.maxrel, rel.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaMemcpyAsync(need.data(), rc.colmask, need.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaStreamSynchronize(st));
-      int live = 0;
-      for (size_t k = 0; k < rel.size(); ++k) {
-        if (!need[k]) continue;
-        if (rel[k] < 0.5 * best[k]) { best[k] = rel[k]; stall[k] = 0; }
-        else ++stall[k];
-        if (stall[k] >= o.stall_sweeps) need[k] = 0;
-        live += need[k];
-      }
-      if (live == 0) break;
-      CBS_CUDA(cudaMemcpyAsync(rc.colmask, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-      CBS_TRY(b32.replace(rc.R, rc.colmask, st));
-    }
-    CBS_CUDA(cudaMemcpyAsync(it_tmp.data(), b32.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), b32.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+  // One Krylov sequence per (point, column) for all n_e energies of the batch (systems
+  // ordered e * n_pt + j as in zs/Es); seed energy: the highest of the batch.  FP64: the
+  // family in FP64.  CBS_FP32_REFINE: the family in complex64 down to family_tol, then the
+  // FP64 solutions are refined per energy as in refine().  The per-energy refinement runs
+  // on groups of energies sized to the free device memory.
+  template <typename R>
+  cbs_status run_family(MultiShift<R> &fam, const HamView &H_, int n_e, int n_pt, int L_,
+                        const double2 *z1, const double *energies_h, const double2 *zs_,
+                        const double *Es_, const double2 *B_, const cbs_options &o, cudaStream_t st) {
+    H = H_; zs = zs_; Es = Es_; B = B_;
+    init_stats(n_e * n_pt, L_);
+    fam.seed.profile = o.profile != 0;
+    double E0 = energies_h[0];
+    for (int e = 1; e < n_e; ++e) E0 = std::max(E0, energies_h[e]);
+    std::vector<double> sig(n_e);
+    for (int e = 0; e < n_e; ++e) sig[e] = energies_h[e] - E0;
+    const bool mixed = sizeof(R) == sizeof(float);
+    const double ftol = mixed ? std::max(o.tol, o.family_tol > 0 ? o.family_tol : 1e-6) : o.tol;
+    fam.seed.apply32 = o.precision == CBS_FP64_APPLY32;
+    CBS_TRY(fam.alloc(H, n_pt, n_e, L));
+    fam.group_need = stop_need(o, n_pt);
+    CBS_TRY(fam.init(z1, E0, sig.data(), B, ftol, st));
+    int done = 0;
+    CBS_TRY(fam.iterate(o.max_iter, o.check_every, st, &done));
+    std::vector<int> fl_tmp((size_t)n * L);
+    CBS_CUDA(cudaMemcpyAsync(iters.data(), fam.siters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), fam.sflags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
     CBS_CUDA(cudaStreamSynchronize(st));
-    for (size_t k = 0; k < iters.size(); ++k) {
-      iters[k] = it_tmp[k];
-      flags[k] |= (fl_tmp[k] & 2);
+    for (size_t k = 0; k < flags.size(); ++k) flags[k] |= (fl_tmp[k] & (2 | 64));
+    double oseed = 0;
+    if (o.profile) CBS_TRY(fam.seed.prof_outputs(st, &oseed));
+    const int ti = mixed ? CBS_C64 : CBS_C128;
+    prof_ms[ti] += fam.seed.prof_ms;
+    prof_launches[ti] += fam.seed.prof_launches;
+    prof_outputs[ti] += oseed;
+    double upd_cols = 0;
+    if (o.profile) CBS_TRY(fam.update_columns(st, &upd_cols));
+    prof_ms[2] += fam.upd_ms;
+    prof_launches[2] += fam.upd_launches;
+    prof_outputs[2] += upd_cols * (double)H.n;
+    fam.release();
+    const size_t vbytes = (size_t)2 * n * H.n * L * sizeof(double2);
+    if (mixed) {
+      // FP64 solutions from the complex64 ones
+      CBS_TRY(ybuf.alloc(vbytes));
+      Y = ybuf.as<double2>();
+      CBS_CUDA(cudaMemsetAsync(Y, 0, vbytes, st));
+      CBS_TRY(launch_accumulate((int64_t)2 * n * H.n * L, Y, (const float2 *)fam.X, st));
+      fam.release_x();
+    } else {
+      Y = (double2 *)fam.X;   // owned by fam until the solver is destroyed
     }
-    CBS_TRY(collect_profile(st));
-    if (unconv > 0) CBS_TRY(rc.run(H, Y, B, b32.tw, b32.E, o.tol, st, &unconv));   // full mask
-    if (unconv > 0) {
-      // FP64 continuation for the columns left: BiCG on P(z) D = R, P(z)^dagger D~ = R~
-      // to tol relative to the original right-hand side, then Y += D
-      b32.release();
-      CBS_TRY(b64.alloc(H, n, L));
-      CBS_TRY(b64.set_systems(zs, Es, st));
-      CBS_TRY(b64.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
-                       rc.colmask, 0.5 * o.tol, 0.0, st, rc.bn2));
-      int done = 0;
-      CBS_TRY(b64.iterate(o.tol, o.max_iter, o.check_every, st, &done));
-      CBS_TRY(launch_accumulate((int64_t)2 * n * H.n * L, Y, b64.x, st));
-      CBS_TRY(rc.run(H, Y, B, b64.tw, b64.E, o.tol, st, &unconv));
-      CBS_CUDA(cudaMemcpyAsync(it_tmp.data(), b64.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CBS_CUDA(cudaMemcpyAsync(fl_tmp.data(), b64.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
+    // per-energy refinement in groups of energies that fit in free memory
+    size_t free_b = 0, total_b = 0;
+    CBS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t per_e = (size_t)n_pt * (bytes_per_system(H, L, o.precision) + (size_t)2 * H.n * L * 16) +
+                         (size_t)2 * n_pt * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * 16 * 2;
+    const int grp = std::max(1, std::min(n_e, (int)((free_b * 8 / 10) / std::max<size_t>(per_e, 1))));
+    const size_t blk = (size_t)H.n * L;
+    for (int g0 = 0; g0 < n_e; g0 += grp) {
+      const int ge = std::min(grp, n_e - g0);
+      ShiftedSolver sub;
+      sub.H = H;
+      sub.zs = zs + (size_t)g0 * n_pt;
+      sub.Es = Es + (size_t)g0 * n_pt;
+      sub.B = B;
+      sub.init_stats(ge * n_pt, L);
+      const size_t sn = (size_t)sub.n;
+      for (size_t k = 0; k < sn * L; ++k) sub.flags[k] = flags[(size_t)g0 * n_pt * L + k];
+      CBS_TRY(sub.ybuf.alloc(2 * sn * blk * sizeof(double2)));
+      sub.Y = sub.ybuf.as<double2>();
+      const size_t off = (size_t)g0 * n_pt;
+      CBS_CUDA(cudaMemcpyAsync(sub.Y, Y + off * blk, sn * blk * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      CBS_CUDA(cudaMemcpyAsync(sub.Y + sn * blk, Y + ((size_t)n + off) * blk, sn * blk * sizeof(double2),
+                               cudaMemcpyDeviceToDevice, st));
+      CBS_TRY(sub.refine(o, st));
+      CBS_CUDA(cudaMemcpyAsync(Y + off * blk, sub.Y, sn * blk * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      CBS_CUDA(cudaMemcpyAsync(Y + ((size_t)n + off) * blk, sub.Y + sn * blk, sn * blk * sizeof(double2),
+                               cudaMemcpyDeviceToDevice, st));
       CBS_CUDA(cudaStreamSynchronize(st));
-      for (size_t k = 0; k < iters.size(); ++k) {
-        iters[k] += it_tmp[k];
-        flags[k] |= (fl_tmp[k] & 2);
+      for (size_t k = 0; k < sn * L; ++k) {
+        iters[off * L + k] += sub.iters[k];
+        flags[off * L + k] = sub.flags[k];
+        maxrel[off * L + k] = sub.maxrel[k];
       }
-      fp64_continued = true;
+      sweeps = std::max(sweeps, sub.sweeps);
+      fp64_continued = fp64_continued || sub.fp64_continued;
+      for (int t = 0; t < 3; ++t) {
+        prof_ms[t] += sub.prof_ms[t];
+        prof_launches[t] += sub.prof_launches[t];
+        prof_outputs[t] += sub.prof_outputs[t];
+      }
     }
-    std::vector<int> mask((size_t)n * L);
-    CBS_CUDA(cudaMemcpyAsync(maxrel.data(), rc.maxrel, (size_t)n * L * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CBS_CUDA(cudaMemcpyAsync(mask.data(), rc.colmask, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CBS_CUDA(cudaStreamSynchronize(st));
-    for (size_t k = 0; k < mask.size(); ++k)
-      if (mask[k]) flags[k] |= 1;
-    return collect_profile(st);
+    return CBS_OK;
   }
 };
 
@@ -415,11 +557,11 @@ static cbs_status check_opts(const cbs_options *opt, cbs_options *o) {
   if (opt) *o = *opt;
   else cbs_options_default(o);
   if (!(o->tol > 0) || !(o->delta > 0) || !(o->rho_max > 0) || o->max_iter < 1 ||
-      (o->precision != CBS_FP64 && o->precision != CBS_FP32_REFINE) ||
+      (o->precision != CBS_FP64 && o->precision != CBS_FP32_REFINE && o->precision != CBS_FP64_APPLY32) ||
       (o->extraction != CBS_HANKEL && o->extraction != CBS_RR) || !(o->inner_tol > 0) ||
       o->max_sweeps < 0 || o->inner_max_iter < 1 || o->stall_sweeps < 1 ||
-      (o->multi_shift != 0 && o->multi_shift != 1) ||
-      (o->multi_shift && o->precision != CBS_FP64)) {
+      (o->multi_shift != 0 && o->multi_shift != 1) || o->family_tol < 0 || o->family_tol >= 1 ||
+      !(o->stop_fraction > 0 && o->stop_fraction <= 1.0) || o->points_per_wave < 0) {
     set_error("invalid cbs_options");
     return CBS_EINVAL;
   }
@@ -447,6 +589,7 @@ extern "C" cbs_status cbs_solve_shifted(const cbs_hamiltonian *h, int n_sys, con
   double *Es = (double *)(zs + n_sys);
   CBS_CUDA(cudaMemcpyAsync(zs, z, (size_t)n_sys * sizeof(double2), cudaMemcpyHostToDevice, st));
   CBS_CUDA(cudaMemcpyAsync(Es, E, (size_t)n_sys * sizeof(double), cudaMemcpyHostToDevice, st));
+  CBS_TRY(check_finite_block((int64_t)h->v.n * L, (const double2 *)B, "cbs_solve_shifted", st));
   ShiftedSolver S;
   CBS_TRY(S.run(h->v, n_sys, L, zs, Es, (const double2 *)B, o, st));
   const size_t blk = (size_t)n_sys * h->v.n * L * sizeof(double2);
@@ -492,6 +635,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
   CBS_TRY(vbuf.alloc((size_t)N * L * sizeof(double2)));
   double2 *dV = vbuf.as<double2>();
   CBS_CUDA(cudaMemcpyAsync(dV, V, (size_t)N * L * sizeof(double2), cudaMemcpyDefault, st));
+  CBS_TRY(check_finite_block((int64_t)N * L, dV, "cbs_solve", st));
   // contour
   DevBuf cbuf;
   CBS_TRY(cbuf.alloc((size_t)n_int * (4 * M + 1) * sizeof(double2) + (size_t)n_e * sizeof(double) + 512));
@@ -504,51 +648,107 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
   // energies per batch from free memory
   size_t free_b = 0, total_b = 0;
   CBS_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const size_t per_sys = ShiftedSolver::bytes_per_system(H, L, o.precision) +
-                         (size_t)2 * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * 16 * 2;
-  const size_t per_e = per_sys * n_int + (size_t)N * nLM * 16 + (size_t)4 * nLM * nLM * 16 * 6;
-  int nb = o.energies_per_batch > 0 ? o.energies_per_batch : (int)std::max<size_t>(1, (free_b * 6 / 10) / per_e);
-  nb = std::min(nb, n_e);
+  // Energies per batch (nb) and quadrature points per wave (nw).  A batch's moments S_k,
+  // mu_k are accumulated over waves of points, each wave solved and then released, so the
+  // solver state scales with nb * nw and only the moments with nb.  Preferred: every point in
+  // one wave and as many energies as fit; when not even one energy's points fit at once,
+  // all energies (or as many as fit) with as many points per wave as fit.
+  const size_t v16 = (size_t)N * L * 16;
+  const size_t dsz = (size_t)2 * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * 16 * 2;
+  const size_t per_sys = ShiftedSolver::bytes_per_system(H, L, o.precision) + dsz;
+  const size_t extract_e = (size_t)N * nLM * 16 + (size_t)4 * nLM * nLM * 16 * 6;
+  auto peak = [&](size_t ne_, size_t nw_) -> size_t {
+    const size_t pairs = ne_ * nw_;
+    size_t solve;
+    if (o.multi_shift) {
+      const size_t vr = o.precision != CBS_FP32_REFINE ? v16 : v16 / 2;
+      const size_t fam = pairs * ShiftedSolver::family_bytes_per_energy(H, 1, L, o.precision) +
+                         nw_ * (2 * 4 * vr + dsz);                        // + seed per point
+      const size_t ref = pairs * 2 * v16 + nw_ * (per_sys + 2 * v16);   // Y + one energy's refinement
+      solve = std::max(fam, ref);
+    } else {
+      solve = pairs * per_sys;
+    }
+    return solve + ne_ * extract_e + 2 * pairs * 8 * L * L * 16;
+  };
+  const size_t usable = free_b * 6 / 10;
+  int nb = 0, nw = n_int;
+  if (o.energies_per_batch > 0) nb = std::min(o.energies_per_batch, n_e);
+  if (o.points_per_wave > 0) nw = std::min(o.points_per_wave, n_int);
+  if (nb == 0) {
+    for (int t = n_e; t >= 1; --t)
+      if (peak(t, nw) <= usable) { nb = t; break; }
+  }
+  if (nb == 0) {                   // not even one energy with these points: waves of points
+    nb = o.energies_per_batch > 0 ? nb : n_e;
+    if (nb == 0) nb = n_e;
+    while (true) {
+      int w = 0;
+      for (int t = nw; t >= 1; --t)
+        if (peak(nb, t) <= usable) { w = t; break; }
+      if (w > 0 || nb == 1) { nw = std::max(w, 1); break; }
+      nb = (nb + 1) / 2;
+    }
+  }
+  nb = std::max(1, std::min(nb, n_e));
 
   cbs_status ret = CBS_OK;
   for (int e0 = 0; e0 < n_e; e0 += nb) {
     const int ne = std::min(nb, n_e - e0);
-    const int nsys = ne * n_int;
-    DevBuf sysb;
-    CBS_TRY(sysb.alloc((size_t)nsys * (sizeof(double2) + sizeof(double)) + 256));
-    double2 *zs = sysb.as<double2>();
-    double *Es = (double *)(zs + nsys);
-    k_expand_systems<<<ceil_div(nsys, 128), 128, 0, st>>>(ne, n_int, z1, dE + e0, zs, Es); cbs::count_launches(1);
-    CBS_CUDA(cudaGetLastError());
-    // ---- step 1: shifted solves
-    ShiftedSolver S;
-    if (o.multi_shift && o.precision == CBS_FP64)
-      CBS_TRY(S.run_family(H, ne, n_int, L, z1, energies + e0, zs, Es, dV, o, st));
-    else
-      CBS_TRY(S.run(H, nsys, L, zs, Es, dV, o, st));
-    for (int t = 0; t < 3; ++t) {
-      res->prof_ms[t] += S.prof_ms[t];
-      res->prof_launches[t] += S.prof_launches[t];
-      res->prof_outputs[t] += S.prof_outputs[t];
-    }
-    CBS_TRY(lap(&res->ms_solve));
-    // ---- step 2: moments
+    // per (energy, point, column) statistics of the batch, gathered over the waves
+    std::vector<int> b_iters((size_t)ne * n_int * L, 0), b_flags((size_t)ne * n_int * L, 0);
+    std::vector<double> b_maxrel((size_t)ne * n_int * L, 0.0);
+    int b_sweeps = 0;
+    bool b_fp64 = false;
     DevBuf mbuf;
     const int nch = vhy_chunks(N);
     const size_t s_bytes = (size_t)ne * N * nLM * sizeof(double2);
     const size_t mu_bytes = (size_t)ne * 2 * M * L * L * sizeof(double2);
-    const size_t part_bytes = (size_t)2 * nsys * nch * L * L * sizeof(double2);
+    const size_t part_bytes = (size_t)2 * ne * nw * nch * L * L * sizeof(double2);
     CBS_TRY(mbuf.alloc(s_bytes + mu_bytes + part_bytes + 1024));
     double2 *Sm = mbuf.as<double2>();
     double2 *mu = (double2 *)((char *)Sm + ((s_bytes + 255) & ~(size_t)255));
     double2 *part = (double2 *)((char *)mu + ((mu_bytes + 255) & ~(size_t)255));
-    CBS_TRY(launch_moments(nsys, ne, n_int, M, N, L, S.Y, coef, Sm, st));
-    CBS_TRY(launch_mu(nsys, ne, n_int, M, N, L, dV, S.Y, coef, part, mu, st));
-    CBS_TRY(lap(&res->ms_moments));
-    // free the solver state before the extraction
-    S.b64.release();
-    S.b32.release();
-    S.ms.release();
+    for (int j0 = 0; j0 < n_int; j0 += nw) {
+      const int nwv = std::min(nw, n_int - j0);
+      const int nsys = ne * nwv;
+      DevBuf sysb;
+      CBS_TRY(sysb.alloc((size_t)nsys * (sizeof(double2) + sizeof(double)) + 256));
+      double2 *zs = sysb.as<double2>();
+      double *Es = (double *)(zs + nsys);
+      k_expand_systems<<<ceil_div(nsys, 128), 128, 0, st>>>(ne, nwv, z1 + j0, dE + e0, zs, Es); cbs::count_launches(1);
+      CBS_CUDA(cudaGetLastError());
+      // ---- step 1: shifted solves of this wave's points
+      ShiftedSolver S;
+      S.group = nwv;
+      if (o.multi_shift && o.precision != CBS_FP32_REFINE)
+        CBS_TRY(S.run_family(S.ms, H, ne, nwv, L, z1 + j0, energies + e0, zs, Es, dV, o, st));
+      else if (o.multi_shift)
+        CBS_TRY(S.run_family(S.ms32, H, ne, nwv, L, z1 + j0, energies + e0, zs, Es, dV, o, st));
+      else
+        CBS_TRY(S.run(H, nsys, L, zs, Es, dV, o, st));
+      for (int t = 0; t < 3; ++t) {
+        res->prof_ms[t] += S.prof_ms[t];
+        res->prof_launches[t] += S.prof_launches[t];
+        res->prof_outputs[t] += S.prof_outputs[t];
+      }
+      for (int e = 0; e < ne; ++e)
+        for (int jj = 0; jj < nwv; ++jj)
+          for (int c = 0; c < L; ++c) {
+            const size_t src = ((size_t)e * nwv + jj) * L + c;
+            const size_t dst = ((size_t)e * n_int + j0 + jj) * L + c;
+            b_iters[dst] = S.iters[src];
+            b_flags[dst] = S.flags[src];
+            b_maxrel[dst] = S.maxrel[src];
+          }
+      b_sweeps = std::max(b_sweeps, S.sweeps);
+      b_fp64 = b_fp64 || S.fp64_continued;
+      CBS_TRY(lap(&res->ms_solve));
+      // ---- step 2: this wave's share of the moments
+      CBS_TRY(launch_moments(nsys, ne, nwv, j0, M, N, L, S.Y, coef, Sm, j0 > 0, st));
+      CBS_TRY(launch_mu(nsys, ne, nwv, j0, M, N, L, dV, S.Y, coef, part, mu, j0 > 0, st));
+      CBS_TRY(lap(&res->ms_moments));
+    }
     // ---- step 3: extraction (Hankel SVD, reduced eigenproblem, vectors, residuals)
     const int n = nLM;   // order of the block Hankel matrices
     const size_t nn = (size_t)n * n;
@@ -608,16 +808,16 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
       for (int j = 0; j < n_int; ++j)
         for (int c = 0; c < L; ++c) {
           const size_t k = ((size_t)e * n_int + j) * L + c;
-          R.iters[(size_t)j * L + c] = S.iters[k];
-          mx = std::max(mx, S.iters[k]);
-          fl |= S.flags[k];
-          mr = std::max(mr, S.maxrel[k]);
+          R.iters[(size_t)j * L + c] = b_iters[k];
+          mx = std::max(mx, b_iters[k]);
+          fl |= b_flags[k];
+          mr = std::max(mr, b_maxrel[k]);
         }
       R.st.max_iters = mx;
-      R.st.sweeps = S.sweeps;
+      R.st.sweeps = b_sweeps;
       R.st.max_solve_residual = mr;
       R.st.flags = (fl & 3) | (m == n ? 4 : 0) | (hsmall[2 * ne + e] ? 8 : 0) | (hsmall[3 * ne + e] ? 16 : 0) |
-                   (S.fp64_continued ? 32 : 0);
+                   (b_fp64 ? 32 : 0) | (fl & 64);
       if (fl & 2) ret = (ret == CBS_OK ? CBS_EBREAKDOWN : ret);
       else if (fl & 1) ret = (ret == CBS_OK ? CBS_ENOCONV : ret);
       else if (m == n && ret == CBS_OK) ret = CBS_WRANK;
@@ -743,6 +943,10 @@ extern "C" cbs_status cbs_solve(const cbs_hamiltonian *h, const double *energies
   }
   cbs_options o;
   CBS_TRY(check_opts(opt, &o));
+  if (o.stop_fraction < 1.0 && contour->n_int > 1024) {
+    set_error("cbs_solve: stop_fraction < 1 needs n_int <= 1024");
+    return CBS_EINVAL;
+  }
   StreamGuard sg;
   CBS_TRY(sg.open(o.stream));
   cbs_result *res = new (std::nothrow) cbs_result();

@@ -89,3 +89,29 @@ def test_frobenius_c2():
     H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
     op = CellOperator(wl.grid, wl.vloc, wl.projectors)
     assert np.allclose(H.norms(-0.2), op.frobenius(-0.2), rtol=1e-11, atol=0)
+
+
+def test_set_vloc_in_place():
+    """cbs_hamiltonian_set_vloc: a handle whose V_loc was replaced (from a device tensor)
+    applies P(z) and reports norms exactly as a handle built with that V_loc; a non-finite
+    V_loc is rejected and leaves the handle unchanged."""
+    torch = need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = small_cases()[1]
+    rng = np.random.default_rng(9)
+    v2 = wl.vloc + 0.1 * rng.standard_normal(wl.vloc.shape)
+    Ha = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    Hb = cbs.Hamiltonian(wl.grid, v2, wl.projectors)
+    Ha.set_vloc(torch.from_numpy(v2).cuda())
+    X = torch.from_numpy(wl.V[None].copy()).cuda().contiguous()
+    for dt in (torch.complex128, torch.complex64):
+        Xd = X.to(dt)
+        ya = cbs.apply(Ha, [1.7 + 0.4j], 0.2, Xd)
+        yb = cbs.apply(Hb, [1.7 + 0.4j], 0.2, Xd)
+        assert torch.equal(ya, yb)
+    assert np.allclose(Ha.norms(0.2), Hb.norms(0.2), rtol=1e-13)
+    bad = v2.copy()
+    bad[4] = np.inf
+    with pytest.raises(cbs.CbsError):
+        Ha.set_vloc(bad)
+    assert torch.equal(cbs.apply(Ha, [1.7 + 0.4j], 0.2, X), cbs.apply(Hb, [1.7 + 0.4j], 0.2, X))

@@ -272,14 +272,26 @@ def test_solve_multishift_single_energy_and_rr():
                                                      tol=1e-12), 1e-10)
 
 
-def test_multishift_needs_fp64():
-    """multi_shift is defined for the FP64 form only; the mixed form rejects it."""
+def test_solve_multishift_mixed_tiny():
+    """Shifted family in complex64 (multi_shift = 1 with CBS_FP32_REFINE): the family runs to
+    family_tol, then every energy is refined with complex64 BiCG and FP64 reliable updates;
+    eigenpairs and moments of every energy against the oracle's per-energy FP64 run."""
     need_gpu()
     from paper_1709_09347_gb300 import cbs
-    wl = small_cases()[0]
+    wl = synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3,
+                             L=12, M=8, n_int=32, energies=(0.2, -0.3, 0.05))
     H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
-    with pytest.raises(cbs.CbsError):
-        cbs.solve(H, [0.1], 0.5, 8, wl.L, 2, wl.V, cbs.options(precision="fp32_refine", multi_shift=1))
+    res = cbs.solve(H, wl.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=1e-12, multi_shift=1, precision="fp32_refine"))
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    for e, E in enumerate(wl.energies):
+        ref = ss.ss_hankel(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12, keep_moments=True)
+        r = res.energies[e]
+        _compare(r, ref, 1e-9)
+        assert r["max_solve_residual"] <= 1e-12
+        for k in range(2 * wl.M):
+            scale = np.max(np.abs(ref.mu[k]))
+            assert np.max(np.abs(r["mu"][k] - ref.mu[k])) <= 100 * 1e-12 * (1 / wl.lambda_min) ** (k + 1) * scale
 
 
 def test_scan_batches_and_branches():
@@ -332,3 +344,85 @@ def test_bench_configuration_properties():
         assert len(res.energies[i]["lam"]) == len(ref)
         worst, un_f, un_r = match(res.energies[i]["lam"], ref, 1e-6)
         assert not un_f and not un_r
+
+
+@pytest.mark.parametrize("multi_shift", [0, 1])
+def test_stop_fraction_load_balance_rule(multi_shift):
+    """The load-balance rule of §3.3 (stop_fraction = 0.5: once more than half of an
+    energy's quadrature points have converged, BiCG stops at the others): no point runs
+    longer than in the full run, the stopped columns carry flag bit 6 and are not reported
+    as unconverged, and every kept pair still passes the residual filter (recomputed by the
+    oracle).  stop_fraction = 1 reproduces the full run."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = synth.workload("c1")
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, None)
+    E = [0.3, 0.6]
+    full = cbs.solve(H, E, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                     cbs.options(tol=1e-12, multi_shift=multi_shift))
+    half = cbs.solve(H, E, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                     cbs.options(tol=1e-12, multi_shift=multi_shift, stop_fraction=0.5))
+    same = cbs.solve(H, E, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                     cbs.options(tol=1e-12, multi_shift=multi_shift, stop_fraction=1.0))
+    op = CellOperator(wl.grid, wl.vloc, None)
+    assert half.status in (cbs.CBS_OK, cbs.CBS_WRANK)
+    for e, Ee in enumerate(E):
+        f, h, s1 = full.energies[e], half.energies[e], same.energies[e]
+        assert np.array_equal(s1["iters"], f["iters"]) and len(s1["lam"]) == len(f["lam"])
+        # per point: the iterations of its slowest column never exceed the full run's
+        assert np.all(h["iters"].max(axis=1) <= f["iters"].max(axis=1))
+        per_point = f["iters"].max(axis=1)
+        if np.sum(per_point < per_point.max()) > wl.n_int // 2:
+            assert h["flags"] & 64
+        assert not h["flags"] & 1
+        if len(h["lam"]):
+            rr = ss.residuals(op, Ee, h["lam"], h["vectors"], op.frobenius(Ee))
+            assert np.all(rr <= 1e-8)
+
+
+@pytest.mark.parametrize("form", [dict(), dict(multi_shift=1), dict(multi_shift=1, precision="fp32_refine")])
+def test_points_in_waves(form):
+    """Quadrature points solved in waves (points_per_wave = 5 of N_int = 32, the last wave
+    ragged), the moments accumulated wave by wave: moments and eigenvalues as with every
+    point in one wave, and as the oracle's."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3,
+                             L=12, M=8, n_int=32, energies=(0.2, -0.3))
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    one = cbs.solve(H, wl.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V, cbs.options(tol=1e-12, **form))
+    wav = cbs.solve(H, wl.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=1e-12, points_per_wave=5, **form))
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    lam_tol = 1e-9 if form.get("precision") == "fp32_refine" else 1e-10
+    for e, E in enumerate(wl.energies):
+        a, b = one.energies[e], wav.energies[e]
+        for k in range(2 * wl.M):
+            scale = np.max(np.abs(a["mu"][k]))
+            assert np.max(np.abs(a["mu"][k] - b["mu"][k])) <= 1e-9 * (1 / wl.lambda_min) ** (k + 1) * scale
+        assert b["iters"].shape == a["iters"].shape and (b["iters"] > 0).all()
+        _compare(b, ss.ss_hankel(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12), lam_tol)
+
+
+@pytest.mark.parametrize("multi_shift", [0, 1])
+def test_solve_fp64_apply32_tiny(multi_shift):
+    """FP64 BiCG with the operator applied in complex64 (CBS_FP64_APPLY32), the columns whose
+    FP64 true residual misses tol continued the same way: every solve reaches tol on the FP64
+    true residual, and eigenvalues and moments match the oracle's FP64 run."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3,
+                             L=12, M=8, n_int=32, energies=(0.2, -0.3, 0.05))
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    res = cbs.solve(H, wl.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=1e-12, multi_shift=multi_shift, precision="fp64_apply32"))
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    for e, E in enumerate(wl.energies):
+        ref = ss.ss_hankel(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12, keep_moments=True)
+        r = res.energies[e]
+        _compare(r, ref, 1e-9)
+        assert r["max_solve_residual"] <= 1e-12
+        assert not r["flags"] & 1
+        for k in range(2 * wl.M):
+            scale = np.max(np.abs(ref.mu[k]))
+            assert np.max(np.abs(r["mu"][k] - ref.mu[k])) <= 100 * 1e-12 * (1 / wl.lambda_min) ** (k + 1) * scale

@@ -79,3 +79,54 @@ def test_ss_tiny_projectors_vs_dense():
         rr = ss.ss_rayleigh_ritz(op, E, wl.lambda_min, wl.n_int, wl.V, wl.M, tol=1e-12)
         assert _check_vs_dense(op, E, rr, wl.lambda_min) < 1e-8
         assert len(rr.lam) == len(res.lam)
+
+
+def test_normalise_phase_convention():
+    """A9: unit 2-norm, largest-modulus entry real and positive, and the column equal to
+    the input times a scalar.  Worked by hand: x = (1, 3i, -2) has norm sqrt(14) and its
+    largest entry 3i; multiplying by -i/sqrt(14) makes that entry 3/sqrt(14)."""
+    X = np.array([[1.0, 2.0 - 2.0j], [3.0j, 0.5], [-2.0, -1.0j]])
+    got = ss.normalise(X)
+    s = np.sqrt(14.0)
+    want0 = np.array([-1.0j, 3.0, 2.0j]) / s
+    assert np.allclose(got[:, 0], want0, rtol=0, atol=1e-15)
+    # second column: |2-2i| = sqrt(8) is the largest, norm sqrt(8 + 0.25 + 1) = sqrt(9.25);
+    # the phase factor is conj(2-2i)/sqrt(8) = (1+i)/sqrt(2)
+    n1 = np.sqrt(9.25)
+    ph = (1.0 + 1.0j) / np.sqrt(2.0)
+    want1 = np.array([2.0 - 2.0j, 0.5, -1.0j]) * ph / n1
+    assert np.allclose(got[:, 1], want1, rtol=0, atol=1e-15)
+    assert abs(got[0, 1].imag) < 1e-15 and got[0, 1].real > 0
+    assert np.allclose(np.linalg.norm(got, axis=0), 1.0, atol=1e-15)
+
+
+def test_filter_sort_order_ring_and_k():
+    """A8/A10: only lambda strictly inside lambda_min < |lambda| < 1/lambda_min with
+    rho <= rho_max survive; the order is |lambda| ascending, then arg(lambda) in
+    (-pi, pi] ascending; k = (arg lambda - i ln|lambda|)/a.  Expected values written out
+    by hand for a = 2 and lambda_min = 0.5."""
+    lam = np.array([
+        2.0 * np.exp(0.5j),      # |.| = 2: on the outer circle, dropped (strict inequality)
+        1.0j,                    # |.| = 1, arg  pi/2
+        -1.0 + 0.0j,             # |.| = 1, arg  pi
+        1.0 + 0.0j,              # |.| = 1, arg  0
+        -1.0j,                   # |.| = 1, arg -pi/2
+        0.6 * np.exp(-3.0j),     # |.| = 0.6, arg -3
+        0.6 * np.exp(1.0j),      # |.| = 0.6, arg  1, residual too large: dropped
+        0.4,                     # inside the inner circle: dropped
+        1.5 * np.exp(2.0j),      # |.| = 1.5
+        np.nan,                  # not finite: dropped
+    ])
+    res = np.array([1e-12, 1e-12, 1e-12, 1e-12, 1e-12, 2e-9, 1e-7, 1e-12, 1e-10, 1e-12])
+    X = np.eye(len(lam), dtype=complex)
+    lam_s, k, res_s, Xs = ss.filter_sort(lam, X, res, 0.5, 2.0, 1e-8)
+    want = np.array([0.6 * np.exp(-3.0j), -1.0j, 1.0, 1.0j, -1.0, 1.5 * np.exp(2.0j)])
+    assert np.allclose(lam_s, want, rtol=0, atol=1e-15)
+    assert np.allclose(res_s, [2e-9, 1e-12, 1e-12, 1e-12, 1e-12, 1e-10])
+    want_k = np.array([(-3.0 - 1j * np.log(0.6)) / 2, -np.pi / 4, 0.0, np.pi / 4, np.pi / 2,
+                       (2.0 - 1j * np.log(1.5)) / 2])
+    assert np.allclose(k, want_k, rtol=0, atol=1e-15)
+    # the vectors follow their eigenvalues: unit vector e_i of input index i
+    src = [5, 4, 3, 1, 2, 8]
+    for col, i in enumerate(src):
+        assert abs(Xs[i, col] - 1.0) < 1e-15
