@@ -3,23 +3,23 @@
 
 One step = the whole method (contour, batched shifted BiCG solves with their duals,
 moments, Hankel SVD + reduced eigenproblem, residual filter, k) for the energies of the
-step, through libcbs's C ABI.  Default workload: the 64x64x24 precision cell (8th-order
-FD, 120 atoms with 4 projectors each, lambda_min = 0.3, N_int = 64 per circle, L = 32,
-M = 8, BiCG tolerance 1e-10), on four of its 32 energies in [-0.5, 0.5] Ha, one from each
-quarter of the range (indices 3, 11, 19, 27: the BiCG iteration count grows about
-sixty-fold from the bottom of the range to the top, so the step samples all of it).
+step, through libcbs's C ABI.  Headline workload: the 32x32x16 molecular-crystal cell
+(8th-order FD, 40 atoms with 4 projectors each, all 16 energies in [-0.5, 0.5] Ha,
+lambda_min = 0.5, N_int = 32 per circle, L = 32, M = 8, the paper's BiCG tolerance 1e-10),
+in the form that is fastest at the residual bar: FP64 with one BiCG Krylov sequence per
+quadrature point and column shared by every energy of the step (shifted BiCG,
+P(z, E) = P(z, E0) + (E - E0) I), half the points solved (real V: the conjugate points'
+solutions are the conjugates), columns missing the tolerance on the true residual finished
+per energy.
 
-Forms, all on the same step at the same eigenpair residual bar (rho <= 1e-8):
-  mixed  (headline)  one complex64 BiCG Krylov sequence per quadrature point and column
-                     shared by every energy of the step (shifted BiCG, P(z, E) =
-                     P(z, E0) + (E - E0) I), then per-energy refinement with complex64 BiCG
-                     and FP64 reliable updates to the FP64 tolerance;
-  fp64               the same shifted family in FP64, columns missing the tolerance on the
-                     true residual finished by FP64 BiCG;
-  fp64_per_energy    (--per-energy) one FP64 BiCG per (energy, quadrature point), the
-                     paper's scheme.
+Beside it, on the same step and bar, each timed once: the complex64 shifted family refined
+per energy with complex64 BiCG and FP64 reliable updates ("mixed"), complex64 BiCG per
+(energy, point) with reliable updates ("mixed_per_energy"), FP64 BiCG per (energy, point) as
+in the paper ("fp64_per_energy"), and the FP64 family with the paper's stop-at-half rule
+("fp64_stop_half").  The 64x64x24 precision cell (120 atoms, lambda_min = 0.3, N_int = 64) is
+measured once per form at energy index 19 ("second_workload"): its steps take minutes.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own copy of the
 step (independent problems, no collective on the data path): weak scaling.
@@ -60,7 +60,20 @@ FORMS = {
               "dtype": "c64 shifted-family BiCG + c64/f64 reliable-update refinement"},
     "fp64": {"precision": "fp64", "multi_shift": 1, "dtype": "f64"},
     "fp64_per_energy": {"precision": "fp64", "multi_shift": 0, "dtype": "f64"},
+    "mixed_per_energy": {"precision": "fp32_refine", "multi_shift": 0,
+                         "dtype": "c64 BiCG + f64 reliable updates, one BiCG per (energy, point)"},
+    # the paper's load-balance rule: BiCG stops once over half the points of an energy converged
+    "fp64_stop_half": {"precision": "fp64", "multi_shift": 1, "stop_fraction": 0.5, "dtype": "f64"},
 }
+
+# headline workload and form; forms timed once beside it; a second workload measured once
+# per form in the same run
+DEFAULT_WORKLOAD = "c2"
+DEFAULT_FORM = "fp64"
+DEFAULT_COMPARE = ("mixed", "mixed_per_energy", "fp64_per_energy", "fp64_stop_half")
+SECOND_WORKLOAD = "c3"
+SECOND_ENERGIES = (19,)
+SECOND_FORMS = ("fp64", "mixed", "fp64_stop_half")
 
 # GB300 FP64: 1.25 TFLOP/s nominal (152 SMs x 2.07 GHz x 4 FLOP/clk/SM).
 FP64_PEAK_TFLOPS = 1.25
@@ -183,7 +196,7 @@ def step_energy_indices(wl, spec):
 CPU_SAMPLE = {
     # workload: (energy index with a stored oracle run, BiCG iterations to time per point)
     "c3": (0, "tests/golden/c3_oracle_e00.npz", 12),
-    "c2": (3, "tests/golden/c2_oracle.npz", 12),
+    "c2": (7, "tests/golden/c2_oracle.npz", 12),
 }
 
 
@@ -289,13 +302,16 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="c3")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--energy-index", default="",
                     help="comma-separated energy indices of one step (default per workload)")
-    ap.add_argument("--form", default="mixed", choices=sorted(FORMS), help="headline form")
-    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
-    ap.add_argument("--per-energy", action="store_true",
-                    help="also time one FP64 BiCG per (energy, quadrature point)")
+    ap.add_argument("--form", default=DEFAULT_FORM, choices=sorted(FORMS), help="headline form")
+    ap.add_argument("--compare", default=",".join(DEFAULT_COMPARE),
+                    help="forms timed once beside the headline on the same step ('' = none)")
+    ap.add_argument("--second-workload", default=SECOND_WORKLOAD,
+                    help="a second workload measured once per form in the same run ('' = none)")
+    ap.add_argument("--second-energy-index", default=",".join(map(str, SECOND_ENERGIES)))
+    ap.add_argument("--second-forms", default=",".join(SECOND_FORMS))
     ap.add_argument("--stop-fraction", type=float, default=1.0,
                     help="load-balance rule of the paper (0.5 = stop once over half the points converged)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -322,58 +338,7 @@ def main():
         dist.init_process_group(backend="nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    wl = synth.workload(args.workload)
-    idx = step_energy_indices(wl, args.energy_index)
-    energies = wl.energies[idx]
-    n_e = len(energies)
-    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
-    Vd = torch.from_numpy(wl.V).to(dev).contiguous()
-    # launch shapes of the stencil kernel, tuned once per cell before any timing
-    n_tune = 2 * wl.n_int
-    tune = {"c128": cbs.autotune_apply(H, n_tune, wl.L, torch.complex128),
-            "c64": cbs.autotune_apply(H, n_tune, wl.L, torch.complex64)}
     hbm, hbm_src = _peaks()
-
-    def spmm(n_sys, dtype_name, iters=20):
-        """Operator apply alone, at the seed batch shape of a family (the 2 N_int primal and
-        dual systems), timed with CUDA events on torch's current stream (the stream the
-        kernels are launched on)."""
-        dt = torch.complex64 if dtype_name == "c64" else torch.complex128
-        s = 8 if dtype_name == "c64" else 16
-        rng = np.random.default_rng(3)
-        zs = (np.exp(1j * rng.uniform(0, 2 * np.pi, n_sys)) *
-              np.where(np.arange(n_sys) % 2 == 0, 1 / wl.lambda_min, wl.lambda_min))
-        plan = cbs.ApplyPlan(H, zs, 0.1, wl.L, dt)
-        X = torch.randn(n_sys, wl.grid.n, wl.L, dtype=dt, device=dev)
-        Yo = torch.empty_like(X)
-        for _ in range(3):
-            plan(X, Yo)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(iters):
-            plan(X, Yo)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / iters
-        outputs = n_sys * wl.grid.n * wl.L
-        bpo = apply_bytes_per_output(wl, s)
-        r = {"dtype": dtype_name, "systems": n_sys, "columns": wl.L, "ms_per_launch": ms,
-             "bytes_per_launch": bpo * outputs, "GB_s": bpo * outputs / (ms / 1e3) / 1e9,
-             "peak_GB_s": hbm, "peak_source": hbm_src,
-             "frac": bpo * outputs / (ms / 1e3) / 1e9 / hbm,
-             "TFLOP_s": apply_flops_per_output(wl) * outputs / (ms / 1e3) / 1e12,
-             "note": "gather (projector coefficients) + stencil launch pair"}
-        del X, Yo, plan
-        torch.cuda.empty_cache()
-        return r
-
-    if args.spmm:
-        r = spmm(args.spmm_systems or 2 * wl.n_int, args.spmm_dtype)
-        if rank == 0:
-            print(json.dumps({"spmm": r, "workload": args.workload, "apply_shape": tune}), flush=True)
-        return
 
     def barrier():
         if world > 1:
@@ -386,83 +351,143 @@ def main():
             return float(t.item())
         return x
 
-    def options(form, profile=True):
-        f = FORMS[form]
-        return cbs.options(precision=f["precision"], multi_shift=f["multi_shift"], tol=wl.tol,
-                           delta=wl.delta, profile=1 if profile else 0,
-                           stop_fraction=args.stop_fraction)
+    class Job:
+        """One workload on this GPU: its Hamiltonian, right-hand sides on the device, the
+        energies of one step, and the stencil launch shapes tuned for it."""
 
-    def one_step(form, V=None):
-        return cbs.solve(H, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, Vd if V is None else V,
-                         options(form))
+        def __init__(self, name, spec):
+            self.wl = synth.workload(name)
+            self.idx = step_energy_indices(self.wl, spec)
+            self.energies = self.wl.energies[self.idx]
+            self.n_e = len(self.energies)
+            self.H = cbs.Hamiltonian(self.wl.grid, self.wl.vloc, self.wl.projectors)
+            self.Vd = torch.from_numpy(self.wl.V).to(dev).contiguous()
+            n_tune = 2 * self.wl.n_int
+            self.tune = {"c128": cbs.autotune_apply(self.H, n_tune, self.wl.L, torch.complex128),
+                         "c64": cbs.autotune_apply(self.H, n_tune, self.wl.L, torch.complex64)}
 
-    def timed(form, steps, warmup):
-        for _ in range(warmup):
-            one_step(form)
-        barrier()
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0 = cbs.kernel_launches()
-        results = []
-        with ClockSampler(local) as clk:
-            ev0.record()
-            for _ in range(steps):
-                results.append(one_step(form))
-            ev1.record()
+        def describe(self):
+            wl = self.wl
+            return (f"{wl.name}: {wl.grid.nx}x{wl.grid.ny}x{wl.grid.nz} cell, FD{wl.grid.fd_order}, "
+                    f"{wl.projectors.n_atoms if wl.projectors else 0} atoms x 4 projectors, "
+                    f"{self.n_e} of its {len(wl.energies)} energies per step (indices {self.idx}), "
+                    f"N_int={wl.n_int}, L={wl.L}, M={wl.M}, lambda_min={wl.lambda_min}, "
+                    f"BiCG tol {wl.tol:g}")
+
+        def options(self, form, profile=True):
+            f = FORMS[form]
+            return cbs.options(precision=f["precision"], multi_shift=f["multi_shift"], tol=self.wl.tol,
+                               delta=self.wl.delta, profile=1 if profile else 0,
+                               stop_fraction=f.get("stop_fraction", args.stop_fraction))
+
+        def one_step(self, form):
+            wl = self.wl
+            return cbs.solve(self.H, self.energies, wl.lambda_min, wl.n_int, wl.L, wl.M, self.Vd,
+                             self.options(form))
+
+        def timed(self, form, steps, warmup):
+            for _ in range(warmup):
+                self.one_step(form)
+            barrier()
             torch.cuda.synchronize()
-        launches = cbs.kernel_launches() - l0
-        barrier()
-        ms = max_over_ranks(ev0.elapsed_time(ev1))
-        return ms, results, clk.summary(), launches
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = cbs.kernel_launches()
+            results = []
+            with ClockSampler(local) as clk:
+                ev0.record()
+                for _ in range(steps):
+                    results.append(self.one_step(form))
+                ev1.record()
+                torch.cuda.synchronize()
+            launches = cbs.kernel_launches() - l0
+            barrier()
+            ms = max_over_ranks(ev0.elapsed_time(ev1))
+            return ms, results, clk.summary(), launches
 
-    def rooflines(results, ms_total, form):
-        """Per kernel class, from the CUDA events the library records around every launch of
-        it inside the BiCG graphs during the timed steps: device time, units processed,
-        algorithmic bytes (or flops) per unit, achieved rate against the peak."""
-        out = {}
-        for key, name in (("c64", "k_proj_gather_c64x2 + k_apply_c64x2: complex64 stencil + projector apply"),
-                          ("c128", "k_proj_gather + k_apply_zm<double>: complex128 stencil + projector apply"),
-                          ("shift_update", "k_ms_update: shifted-family direction and solution update")):
-            p = {f: sum(r.profile[key][f] for r in results) for f in ("ms", "launches", "outputs")}
-            if not p["ms"]:
-                continue
-            launches = max(p["launches"], 1)
-            sec = p["ms"] / 1e3
-            rl = {"kernel": name, "units": p["outputs"], "launches": p["launches"],
-                  "avg_launch_ms": p["ms"] / launches, "share_of_step": p["ms"] / ms_total}
-            mixed_family = FORMS[form]["precision"] == "fp32_refine"
-            if key == "c64":
-                bpu = apply_bytes_per_output(wl, 8)
-                ach = p["outputs"] * bpu / sec / 1e9
-                rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
-                          peak_source=hbm_src, bytes_per_unit=bpu, unit_of_work="complex output",
-                          traffic=_traffic("c64_apply", p["outputs"] / launches))
-            elif key == "c128":
-                fpu = apply_flops_per_output(wl)
-                ach = p["outputs"] * fpu / sec / 1e12
-                rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                          frac=ach / FP64_PEAK_TFLOPS, flops_per_unit=fpu, unit_of_work="complex output",
-                          peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
-                          traffic=_traffic("c128_apply", p["outputs"] / launches))
-            elif mixed_family:
-                # per (energy, point, column) triple and grid point: scaled direction and
-                # solution read and written, primal and dual, complex64 (8 x 8 B)
-                bpu = 64
-                ach = p["outputs"] * bpu / sec / 1e9
-                rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
-                          peak_source=hbm_src, bytes_per_unit=bpu,
-                          unit_of_work="(energy, point, column) triple x grid point",
-                          traffic=_traffic("c64_shift_update", p["outputs"] / launches))
-            else:
-                # FP64 family: 16 FP64 FMAs per unit, bound by the FP64 pipe
-                ach = p["outputs"] * 32 / sec / 1e12
-                rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                          frac=ach / FP64_PEAK_TFLOPS, flops_per_unit=32, traffic=None,
-                          unit_of_work="(energy, point, column) triple x grid point",
-                          peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
-                          hbm_GB_s=p["outputs"] * 128 / sec / 1e9)
-            out[key] = rl
-        return out
+        def spmm(self, n_sys, dtype_name, iters=20):
+            """Operator apply alone, at the seed batch shape of a family (the 2 N_int primal and
+            dual systems), timed with CUDA events on torch's current stream (the stream the
+            kernels are launched on)."""
+            wl = self.wl
+            dt = torch.complex64 if dtype_name == "c64" else torch.complex128
+            s = 8 if dtype_name == "c64" else 16
+            rng = np.random.default_rng(3)
+            zs = (np.exp(1j * rng.uniform(0, 2 * np.pi, n_sys)) *
+                  np.where(np.arange(n_sys) % 2 == 0, 1 / wl.lambda_min, wl.lambda_min))
+            plan = cbs.ApplyPlan(self.H, zs, 0.1, wl.L, dt)
+            X = torch.randn(n_sys, wl.grid.n, wl.L, dtype=dt, device=dev)
+            Yo = torch.empty_like(X)
+            for _ in range(3):
+                plan(X, Yo)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(iters):
+                plan(X, Yo)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / iters
+            outputs = n_sys * wl.grid.n * wl.L
+            bpo = apply_bytes_per_output(wl, s)
+            r = {"workload": wl.name, "dtype": dtype_name, "systems": n_sys, "columns": wl.L,
+                 "ms_per_launch": ms, "bytes_per_launch": bpo * outputs,
+                 "GB_s": bpo * outputs / (ms / 1e3) / 1e9, "peak_GB_s": hbm, "peak_source": hbm_src,
+                 "frac": bpo * outputs / (ms / 1e3) / 1e9 / hbm,
+                 "TFLOP_s": apply_flops_per_output(wl) * outputs / (ms / 1e3) / 1e12,
+                 "note": "gather (projector coefficients) + stencil launch pair"}
+            del X, Yo, plan
+            torch.cuda.empty_cache()
+            return r
+
+        def rooflines(self, results, ms_total, form):
+            """Per kernel class, from the CUDA events the library records around every launch
+            of it inside the BiCG graphs during the timed steps: device time, units processed,
+            algorithmic bytes (or flops) per unit, achieved rate against the peak."""
+            wl = self.wl
+            out = {}
+            for key, name in (("c64", "k_proj_gather_c64x2 + k_apply_c64x2: complex64 stencil + projector apply"),
+                              ("c128", "k_proj_gather + k_apply_zm<double>: complex128 stencil + projector apply"),
+                              ("shift_update", "k_ms_update: shifted-family direction and solution update")):
+                p = {f: sum(r.profile[key][f] for r in results) for f in ("ms", "launches", "outputs")}
+                if not p["ms"]:
+                    continue
+                launches = max(p["launches"], 1)
+                sec = p["ms"] / 1e3
+                rl = {"kernel": name, "units": p["outputs"], "launches": p["launches"],
+                      "avg_launch_ms": p["ms"] / launches, "share_of_step": p["ms"] / ms_total}
+                c64_family = FORMS[form]["precision"] == "fp32_refine"
+                if key == "c64":
+                    bpu = apply_bytes_per_output(wl, 8)
+                    ach = p["outputs"] * bpu / sec / 1e9
+                    rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                              peak_source=hbm_src, bytes_per_unit=bpu, unit_of_work="complex output",
+                              traffic=_traffic("c64_apply", p["outputs"] / launches))
+                elif key == "c128":
+                    fpu = apply_flops_per_output(wl)
+                    ach = p["outputs"] * fpu / sec / 1e12
+                    rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                              frac=ach / FP64_PEAK_TFLOPS, flops_per_unit=fpu, unit_of_work="complex output",
+                              peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
+                              traffic=_traffic("c128_apply", p["outputs"] / launches))
+                elif c64_family:
+                    # per (energy, point, column) triple and grid point: scaled direction and
+                    # solution read and written, primal and dual, complex64 (8 x 8 B)
+                    bpu = 64
+                    ach = p["outputs"] * bpu / sec / 1e9
+                    rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                              peak_source=hbm_src, bytes_per_unit=bpu,
+                              unit_of_work="(energy, point, column) triple x grid point",
+                              traffic=_traffic("c64_shift_update", p["outputs"] / launches))
+                else:
+                    # FP64 family: 16 FP64 FMAs per unit, bound by the FP64 pipe
+                    ach = p["outputs"] * 32 / sec / 1e12
+                    rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                              frac=ach / FP64_PEAK_TFLOPS, flops_per_unit=32, traffic=None,
+                              unit_of_work="(energy, point, column) triple x grid point",
+                              peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
+                              hbm_GB_s=p["outputs"] * 128 / sec / 1e9)
+                out[key] = rl
+            return out
 
     def summary(results):
         last = results[-1]
@@ -471,8 +496,8 @@ def main():
         return last, kept, worst, sorted({e["flags"] for e in last.energies})
 
     def lam_agreement(a, b):
-        """Largest relative distance from each eigenvalue of form a to its nearest partner
-        of form b, over the energies where both keep the same count."""
+        """Largest relative distance from each eigenvalue of result a to its nearest partner
+        in result b, over the energies where both keep the same count."""
         worst = 0.0
         for ea, eb in zip(a.energies, b.energies):
             if len(ea["lam"]) != len(eb["lam"]) or not len(ea["lam"]):
@@ -481,31 +506,61 @@ def main():
             worst = max(worst, float(d.max()))
         return worst
 
+    def once(job, form, ref=None, ref_value=None):
+        """One untimed-warm-up-free step of a form, with what 'equal residual' needs: kept
+        counts, largest residual, eigenvalue agreement with a reference result."""
+        msc, resc, clkc, lc = job.timed(form, 1, 0)
+        lastc, keptc, worstc, flagsc = summary(resc)
+        out = {"value": job.n_e * world / (msc / 1e3), "unit": UNIT, "ms_per_step": msc, "steps": 1,
+               "warmup": 0, "dtype": FORMS[form]["dtype"], "kept_per_energy": keptc,
+               "max_residual": worstc, "flags": flagsc,
+               "max_solve_residual": max(e["max_solve_residual"] for e in lastc.energies),
+               "rooflines": job.rooflines(resc, msc, form), "clocks": clkc, "gpu_launches": lc,
+               "stage_ms": {"solve": lastc.ms_solve, "moments": lastc.ms_moments, "extract": lastc.ms_extract}}
+        if ref is not None:
+            out["same_count_as_reference"] = keptc == [len(e["lam"]) for e in ref.energies]
+            out["max_rel_lambda_diff_to_reference"] = lam_agreement(lastc, ref)
+        if ref_value:
+            out["value_over_reference_form"] = out["value"] / ref_value
+        return out, lastc
+
+    job = Job(args.workload, args.energy_index)
+    wl, energies, n_e, idx = job.wl, job.energies, job.n_e, job.idx
+    if args.spmm:
+        r = job.spmm(args.spmm_systems or 2 * wl.n_int, args.spmm_dtype)
+        if rank == 0:
+            print(json.dumps({"spmm": r, "workload": args.workload, "apply_shape": job.tune}), flush=True)
+        return
+
     headline = args.form
-    ms, results, clocks, launches = timed(headline, args.steps, args.warmup)
+    ms, results, clocks, launches = job.timed(headline, args.steps, args.warmup)
     value = args.steps * n_e * world / (ms / 1e3)
     last, kept, worst_res, flags = summary(results)
-    rl = rooflines(results, ms, headline)
+    rl = job.rooflines(results, ms, headline)
     ranked = sorted(rl.values(), key=lambda r: -r["share_of_step"])
     roofline = ranked[0] if ranked else None
     roofline_second = ranked[1] if len(ranked) > 1 else None
 
     compare = {}
-    other = [f for f in ("fp64", "mixed") if f != headline]
-    if args.per_energy and headline != "fp64_per_energy":
-        other.append("fp64_per_energy")
-    if not args.no_compare:
-        for form in other:
-            msc, resc, clkc, lc = timed(form, 1, 0)
-            lastc, keptc, worstc, flagsc = summary(resc)
-            compare[form] = {
-                "value": n_e * world / (msc / 1e3), "unit": UNIT, "ms_per_step": msc, "steps": 1,
-                "warmup": 0, "dtype": FORMS[form]["dtype"], "kept_per_energy": keptc,
-                "same_count_as_headline": keptc == kept, "max_residual": worstc, "flags": flagsc,
-                "max_rel_lambda_diff_to_headline": lam_agreement(lastc, last),
-                "headline_speedup": (value / (n_e * world / (msc / 1e3))),
-                "rooflines": rooflines(resc, msc, form), "clocks": clkc, "gpu_launches": lc,
-                "stage_ms": {"solve": lastc.ms_solve, "moments": lastc.ms_moments, "extract": lastc.ms_extract}}
+    for form in [f for f in args.compare.split(",") if f and f != headline]:
+        compare[form], _ = once(job, form, last, value)
+        compare[form]["headline_over_this"] = value / compare[form]["value"]
+
+    # the same measurement on a second workload, once per form (the first form is the
+    # reference for eigenvalue agreement)
+    second = None
+    if args.second_workload:
+        job2 = Job(args.second_workload, args.second_energy_index)
+        second = {"workload": job2.describe(), "energies": [float(x) for x in job2.energies], "forms": {}}
+        ref2 = ref2_value = None
+        for form in [f for f in args.second_forms.split(",") if f]:
+            second["forms"][form], res2 = once(job2, form, ref2, ref2_value)
+            if ref2 is None:
+                ref2, ref2_value = res2, second["forms"][form]["value"]
+        second["spmm"] = {"c64": job2.spmm(2 * job2.wl.n_int, "c64"),
+                          "c128": job2.spmm(2 * job2.wl.n_int, "c128", iters=3)}
+        del job2
+        torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers: Hamiltonian upload, V upload,
     # solve, results (eigenvalues, k, residuals, eigenvectors) back to the host
@@ -514,9 +569,11 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Hh = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
-        cbs.set_apply_shape(Hh, torch.complex128, tune["c128"]["py"], tune["c128"]["pz"])
-        cbs.set_apply_shape(Hh, torch.complex64, tune["c64"]["py"], tune["c64"]["pz"], tune["c64"]["x2"])
-        r_e2e = cbs.solve(Hh, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V, options(headline, False))
+        cbs.set_apply_shape(Hh, torch.complex128, job.tune["c128"]["py"], job.tune["c128"]["pz"])
+        cbs.set_apply_shape(Hh, torch.complex64, job.tune["c64"]["py"], job.tune["c64"]["pz"],
+                            job.tune["c64"]["x2"])
+        r_e2e = cbs.solve(Hh, energies, wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                          job.options(headline, False))
         Hh.close()
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
@@ -530,7 +587,7 @@ def main():
                "d2h_bytes_per_step": int(d2h), "steps": 1,
                "same_count_as_headline": [len(e["lam"]) for e in r_e2e.energies] == kept}
 
-    spmm_res = {"c64": spmm(2 * wl.n_int, "c64"), "c128": spmm(2 * wl.n_int, "c128", iters=3)}
+    spmm_res = {"c64": job.spmm(2 * wl.n_int, "c64"), "c128": job.spmm(2 * wl.n_int, "c128", iters=3)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -545,21 +602,16 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": f["dtype"], "data": "synthetic",
-            "config": {"workload": (f"{args.workload}: {wl.grid.nx}x{wl.grid.ny}x{wl.grid.nz} cell, "
-                                    f"FD{wl.grid.fd_order}, "
-                                    f"{wl.projectors.n_atoms if wl.projectors else 0} atoms x 4 projectors, "
-                                    f"{n_e} of its {len(wl.energies)} energies per step (indices {idx}), "
-                                    f"N_int={wl.n_int}, L={wl.L}, M={wl.M}, lambda_min={wl.lambda_min}, "
-                                    f"BiCG tol {wl.tol:g}"),
-                       "form": headline, "solver": FORMS[headline],
+            "config": {"workload": job.describe(), "form": headline, "solver": FORMS[headline],
                        "energies": [float(x) for x in energies], "energies_per_step": n_e,
                        "stop_fraction": args.stop_fraction,
                        "l2": "state per step >> L2 (no flush needed)",
                        "kept_per_energy": kept, "max_residual": worst_res, "flags": flags,
-                       "apply_shape": tune},
+                       "max_solve_residual": max(e["max_solve_residual"] for e in last.energies),
+                       "apply_shape": job.tune},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
             "roofline_second_kernel": roofline_second, "cpu_baseline": cpu, "compare": compare,
-            "spmm": spmm_res,
+            "second_workload": second, "spmm": spmm_res,
             "stage_ms_last_step": {"solve": last.ms_solve, "moments": last.ms_moments,
                                    "extract": last.ms_extract, "extract_svd": last.ms_svd,
                                    "extract_reduced_eig": last.ms_reduced,

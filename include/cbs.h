@@ -54,10 +54,8 @@ typedef enum {
 } cbs_status;
 
 /* cbs_options.precision: CBS_FP64 plain FP64 BiCG; CBS_FP32_REFINE complex64 BiCG with FP64
- * reliable updates (residual replacement); CBS_FP64_APPLY32 FP64 BiCG vectors and
- * recurrences with the operator applied in complex64 (FP32 accumulation), the true residual
- * checked with the FP64 operator and the columns above tol continued the same way. */
-enum { CBS_FP64 = 0, CBS_FP32_REFINE = 1, CBS_FP64_APPLY32 = 2 };
+ * reliable updates (residual replacement). */
+enum { CBS_FP64 = 0, CBS_FP32_REFINE = 1 };
 enum { CBS_HANKEL = 0, CBS_RR = 1 };            /* cbs_options.extraction */
 enum { CBS_C128 = 0, CBS_C64 = 1 };             /* element type of vector blocks */
 
@@ -98,7 +96,7 @@ typedef struct {
   double delta;         /* rank cut: keep sigma_i >= delta * sigma_1 (1e-10)              */
   double rho_max;       /* keep eigenpairs with residual rho <= rho_max (1e-8)           */
   int max_iter;         /* BiCG iterations per column (FP64) / per inner solve (20000)   */
-  int precision;        /* CBS_FP64, CBS_FP32_REFINE or CBS_FP64_APPLY32 (see above)     */
+  int precision;        /* CBS_FP64 or CBS_FP32_REFINE (see above)                       */
   int extraction;       /* CBS_HANKEL (Algorithm 1) or CBS_RR (Rayleigh-Ritz)            */
   int check_every;      /* BiCG iterations per CUDA-graph replay between host polls (8)  */
   double inner_tol;     /* complex64 phase ends when ||r|| < inner_tol * max ||r|| since the
@@ -131,6 +129,11 @@ typedef struct {
                            time (the rule above then counts the points of one wave).
                            0 = all points when one energy's fit in memory, else as many as
                            fit (0)                                                          */
+  int conj_points;      /* 1: when every entry of V is real and n_int is even, solve only the
+                           first n_int/2 outer-circle points: the blocks of Eq. (2) are real, so
+                           P(conj z) = conj P(z) and the solutions at the conjugate points
+                           z_{n_int-1-j} = conj(z_j) (and their duals) are the conjugates of the
+                           solved ones (not in the paper).  0: solve every point (1)         */
 } cbs_options;
 
 /* Fill *opt with the defaults given above. */

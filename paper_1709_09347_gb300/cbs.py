@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libcbs.so")
 CBS_OK, CBS_EINVAL, CBS_ENOMEM, CBS_ECUDA, CBS_ENOCONV, CBS_EBREAKDOWN, CBS_ETIMEOUT, CBS_WRANK = range(8)
 STATUS_NAMES = ["CBS_OK", "CBS_EINVAL", "CBS_ENOMEM", "CBS_ECUDA", "CBS_ENOCONV",
                 "CBS_EBREAKDOWN", "CBS_ETIMEOUT", "CBS_WRANK"]
-CBS_FP64, CBS_FP32_REFINE, CBS_FP64_APPLY32 = 0, 1, 2
+CBS_FP64, CBS_FP32_REFINE = 0, 1
 CBS_HANKEL, CBS_RR = 0, 1
 CBS_C128, CBS_C64 = 0, 1
 
@@ -56,7 +56,7 @@ class Options(ct.Structure):
                 ("check_every", ct.c_int), ("inner_tol", ct.c_double), ("max_sweeps", ct.c_int), ("inner_max_iter", ct.c_int), ("stall_sweeps", ct.c_int),
                 ("energies_per_batch", ct.c_int), ("profile", ct.c_int), ("multi_shift", ct.c_int),
                 ("stream", ct.c_void_p), ("family_tol", ct.c_double), ("stop_fraction", ct.c_double),
-                ("points_per_wave", ct.c_int)]
+                ("points_per_wave", ct.c_int), ("conj_points", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -136,7 +136,7 @@ def options(**kw) -> Options:
     load().cbs_options_default(ct.byref(o))
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
-            v = {"fp64": CBS_FP64, "fp32_refine": CBS_FP32_REFINE, "fp64_apply32": CBS_FP64_APPLY32}[v]
+            v = {"fp64": CBS_FP64, "fp32_refine": CBS_FP32_REFINE}[v]
         if k == "extraction" and isinstance(v, str):
             v = {"hankel": CBS_HANKEL, "rr": CBS_RR}[v]
         setattr(o, k, v)

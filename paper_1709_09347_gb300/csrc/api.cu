@@ -54,6 +54,7 @@ extern "C" cbs_status cbs_options_default(cbs_options *o) {
   o->family_tol = 0.0;
   o->stop_fraction = 1.0;
   o->points_per_wave = 0;
+  o->conj_points = 1;
   return CBS_OK;
 }
 

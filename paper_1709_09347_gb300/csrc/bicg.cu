@@ -390,14 +390,11 @@ static void chunking(int64_t N, int L, int *chunk_pts, int *n_chunks) {
 }
 
 template <typename R>
-size_t Bicg<R>::bytes_needed(const HamView &H, int n, int L, bool apply32) {
+size_t Bicg<R>::bytes_needed(const HamView &H, int n, int L) {
   int cp, nc;
   chunking(H.n, L, &cp, &nc);
   const int64_t vec = (int64_t)2 * n * H.n * L * sizeof(C);
   int64_t b = 4 * align256(vec);
-  if (apply32)
-    b += 2 * align256((int64_t)2 * n * H.n * L * sizeof(float2)) +
-         align256((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * sizeof(float2));
   b += align256((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * sizeof(C));
   b += align256((int64_t)2 * n * sizeof(double2)) + align256((int64_t)2 * n * sizeof(double));
   b += 4 * align256((int64_t)n * L * sizeof(double2)) + 6 * align256((int64_t)n * L * sizeof(double));
@@ -410,7 +407,7 @@ template <typename R>
 cbs_status Bicg<R>::alloc(const HamView &H_, int n_, int L_) {
   H = H_; n = n_; L = L_; N = H.n;
   chunking(N, L, &chunk_pts, &n_chunks);
-  bytes = bytes_needed(H, n, L, apply32);
+  bytes = bytes_needed(H, n, L);
   cudaError_t e = cudaMalloc(&block, bytes);
   if (e != cudaSuccess) {
     block = nullptr;
@@ -441,11 +438,6 @@ cbs_status Bicg<R>::alloc(const HamView &H_, int n_, int L_) {
   n_active = (int *)take(256);
   part = (double *)take((int64_t)n * n_chunks * L * 4 * sizeof(double));
   sys_apply = (unsigned long long *)take(256);
-  if (apply32) {
-    p32 = (float2 *)take((int64_t)2 * n * N * L * sizeof(float2));
-    q32 = (float2 *)take((int64_t)2 * n * N * L * sizeof(float2));
-    D32 = (float2 *)take((int64_t)2 * n * (H.n_atoms ? H.n_atoms : 1) * H.np4 * L * sizeof(float2));
-  }
   CBS_CUDA(cudaMemset(sys_apply, 0, sizeof(unsigned long long)));
   return CBS_OK;
 }
@@ -500,48 +492,6 @@ cbs_status Bicg<R>::init(const double2 *B, int64_t bstride, const double2 *Bd, i
   return CBS_OK;
 }
 
-// complex128 <-> complex64 copies of the systems that are still active (per system, over
-// [N][L] blocks)
-__global__ void k_narrow(int64_t per_sys, const double2 *__restrict__ a, float2 *__restrict__ b,
-                         const int *__restrict__ sys_active) {
-  const int s = blockIdx.y;
-  if (sys_active && !sys_active[s]) return;
-  const double2 *as = a + (int64_t)s * per_sys;
-  float2 *bs = b + (int64_t)s * per_sys;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_sys; i += (int64_t)gridDim.x * blockDim.x) {
-    const double2 v = as[i];
-    bs[i] = make_float2((float)v.x, (float)v.y);
-  }
-}
-__global__ void k_widen(int64_t per_sys, const float2 *__restrict__ a, double2 *__restrict__ b,
-                        const int *__restrict__ sys_active) {
-  const int s = blockIdx.y;
-  if (sys_active && !sys_active[s]) return;
-  const float2 *as = a + (int64_t)s * per_sys;
-  double2 *bs = b + (int64_t)s * per_sys;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_sys; i += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = as[i];
-    bs[i] = make_double2(v.x, v.y);
-  }
-}
-
-// q = P(z) p for the 2n systems of a Bicg state: in the state's precision, or (apply32)
-// through complex64 copies
-template <typename R>
-static cbs_status bicg_apply(Bicg<R> &b, const typename CT<R>::T *p, typename CT<R>::T *q, cudaStream_t st) {
-  if (sizeof(R) == sizeof(double) && b.apply32) {
-    const int64_t per = b.N * b.L;
-    dim3 grd((unsigned)std::min<int64_t>(64, (per + 255) / 256), (unsigned)(2 * b.n), 1);
-    k_narrow<<<grd, 256, 0, st>>>(per, (const double2 *)p, b.p32, b.sys_active); cbs::count_launches(1);
-    CBS_CUDA(cudaGetLastError());
-    CBS_TRY_B(apply_P<float>(b.H, 2 * b.n, b.L, b.p32, b.q32, b.tw, false, b.E, b.D32, b.sys_active, st));
-    k_widen<<<grd, 256, 0, st>>>(per, b.q32, (double2 *)q, b.sys_active); cbs::count_launches(1);
-    CBS_CUDA(cudaGetLastError());
-    return CBS_OK;
-  }
-  return apply_P<R>(b.H, 2 * b.n, b.L, p, q, b.tw, false, b.E, b.D, b.sys_active, st);
-}
-
 template <typename R>
 cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st, int kk) {
   dim3 blk = col_block(L);
@@ -551,7 +501,7 @@ cbs_status Bicg<R>::step(double tol, int max_iter, cudaStream_t st, int kk) {
   const bool prof = profile && kk >= 0 && 2 * kk + 1 < n_prof_ev;
   // recorded as real event nodes of the graph (not capture-dependency markers)
   if (prof) CBS_CUDA(cudaEventRecordWithFlags(prof_ev[2 * kk], st, cudaEventRecordExternal));
-  cbs_status s = bicg_apply(*this, p, q, st);
+  cbs_status s = apply_P<R>(H, 2 * n, L, p, q, tw, false, E, D, sys_active, st);
   if (s != CBS_OK) return s;
   if (prof) CBS_CUDA(cudaEventRecordWithFlags(prof_ev[2 * kk + 1], st, cudaEventRecordExternal));
   k_dot_pq<R><<<grd, blk, red_smem(L), st>>>(n, N, L, chunk_pts, n_chunks, p, q, part, sys_active); cbs::count_launches(1);
@@ -906,7 +856,7 @@ cbs_status MultiShift<R>::step(int max_iter, cudaStream_t st, int kk) {
   CBS_CUDA(cudaGetLastError());
   const bool prof = b.profile && kk >= 0 && 2 * kk + 1 < b.n_prof_ev;
   if (prof) CBS_CUDA(cudaEventRecordWithFlags(b.prof_ev[2 * kk], st, cudaEventRecordExternal));
-  cbs_status s = bicg_apply(b, b.p, b.q, st);
+  cbs_status s = apply_P<R>(b.H, 2 * n_pt, L, b.p, b.q, b.tw, false, b.E, b.D, b.sys_active, st);
   if (s != CBS_OK) return s;
   if (prof) CBS_CUDA(cudaEventRecordWithFlags(b.prof_ev[2 * kk + 1], st, cudaEventRecordExternal));
   k_dot_pq<R><<<grd, blk, red_smem(L), st>>>(n_pt, N, L, b.chunk_pts, b.n_chunks, b.p, b.q, b.part, b.sys_active); cbs::count_launches(1);

@@ -44,13 +44,8 @@ struct Bicg {
   // energy (0 = no groups); a group's remaining systems stop once more than group_need of
   // them have stopped
   int group = 0, group_need = 0;
-  // FP64 vectors and recurrences with the operator applied in complex64 (set before alloc;
-  // R = double only): q = P(z) p is formed from p rounded to complex64, with FP32
-  // accumulation, and widened back
-  bool apply32 = false;
-  float2 *p32 = nullptr, *q32 = nullptr, *D32 = nullptr;
 
-  static size_t bytes_needed(const HamView &H, int n, int L, bool apply32 = false);
+  static size_t bytes_needed(const HamView &H, int n, int L);
   cbs_status alloc(const HamView &H, int n, int L);
   void release();
   // Set twists/energies: primal twist z[s], dual twist 1/conj(z[s]); z, E on device.

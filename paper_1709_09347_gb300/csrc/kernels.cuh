@@ -9,13 +9,14 @@ namespace cbs {
 cbs_status launch_contour(int n_int, int M, double lambda_min, double2 *coef, double2 *z1,
                           cudaStream_t st);
 // moments of the solutions of one wave of quadrature points j0 .. j0 + n_w - 1 (systems
-// e * n_w + jj, n = n_e * n_w); accumulate = add to S / mu (later waves)
+// e * n_w + jj, n = n_e * n_w); accumulate = add to S / mu (later waves); mirror = n_int when
+// the conjugate points n_int - 1 - j take conj(Y_j) (real blocks, real V), else 0
 cbs_status launch_moments(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, const double2 *Y,
-                          const double2 *coef, double2 *S, bool accumulate, cudaStream_t st);
+                          const double2 *coef, double2 *S, bool accumulate, int mirror, cudaStream_t st);
 int vhy_chunks(int64_t N);
 cbs_status launch_mu(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, const double2 *V,
                      const double2 *Y, const double2 *coef, double2 *part, double2 *mu,
-                     bool accumulate, cudaStream_t st);
+                     bool accumulate, int mirror, cudaStream_t st);
 
 // dense.cu
 cbs_status launch_hankel(int n_e, int L, int M, const double2 *mu, double2 *T, double2 *Tl,

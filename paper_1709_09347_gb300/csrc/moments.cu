@@ -42,9 +42,13 @@ cbs_status launch_contour(int n_int, int M, double lambda_min, double2 *coef, do
 // S[e][i][k][c] for k < M from the n_w primal (system e*n_w + jj) and dual (n + e*n_w + jj)
 // solutions stored in Y[2n][N][L], n = n_e * n_w, of quadrature points j = j0 + jj; with
 // `accumulate` the wave's sum is added to S (points streamed in waves), else it replaces S.
+// mirror > 0: the solutions at the conjugate point j' = mirror - 1 - j (z_j' = conj(z_j),
+// same for the dual twists) are conj(Y_j), which holds for real blocks and a real V, and
+// enter with their own coefficients.
 template <int MM>
 __global__ void k_moments(int n, int n_w, int j0, int M, int64_t N, int L, const double2 *__restrict__ Y,
-                          const double2 *__restrict__ coef, double2 *__restrict__ S, int accumulate) {
+                          const double2 *__restrict__ coef, double2 *__restrict__ S, int accumulate,
+                          int mirror) {
   const int e = blockIdx.y, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
   const int M2 = 2 * M;
   const int64_t per = (int64_t)py * 4;
@@ -67,6 +71,17 @@ __global__ void k_moments(int n, int n_w, int j0, int M, int64_t N, int L, const
           acc[k] = cfma(a[k], y1, acc[k]);
           acc[k] = cfma(make_double2(-b[k].x, -b[k].y), y2, acc[k]);
         }
+      if (mirror > 0) {
+        const double2 *am = coef + (int64_t)(mirror - 1 - j0 - jj) * 2 * M2;
+        const double2 *bm = am + M2;
+        const double2 y1c = cconj(y1), y2c = cconj(y2);
+#pragma unroll
+        for (int k = 0; k < MM; ++k)
+          if (k < M) {
+            acc[k] = cfma(am[k], y1c, acc[k]);
+            acc[k] = cfma(make_double2(-bm[k].x, -bm[k].y), y2c, acc[k]);
+          }
+      }
     }
 #pragma unroll
     for (int k = 0; k < MM; ++k)
@@ -75,13 +90,13 @@ __global__ void k_moments(int n, int n_w, int j0, int M, int64_t N, int L, const
 }
 
 cbs_status launch_moments(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, const double2 *Y,
-                          const double2 *coef, double2 *S, bool accumulate, cudaStream_t st) {
+                          const double2 *coef, double2 *S, bool accumulate, int mirror, cudaStream_t st) {
   dim3 blk = col_block(L);
   dim3 grd((unsigned)ceil_div(N, (int64_t)blk.y * 4), (unsigned)n_e, 1);
   if (M <= 8)
-    k_moments<8><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, accumulate ? 1 : 0);
+    k_moments<8><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, accumulate ? 1 : 0, mirror);
   else if (M <= 16)
-    k_moments<16><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, accumulate ? 1 : 0);
+    k_moments<16><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, accumulate ? 1 : 0, mirror);
   else {
     set_error("M must be <= 16");
     return CBS_EINVAL;
@@ -133,9 +148,10 @@ __global__ void k_vhy(int64_t N, int L, int n_chunks, const double2 *__restrict_
 }
 
 // mu[e][k][c1][c2] (+)= sum_jj sum_chunks a_{j0+jj,k} G_jj - b_{j0+jj,k} G~_jj over the wave's
-// points
+// points; mirror > 0: plus the conjugate points' terms, whose G = V^dagger conj(Y_j) is
+// conj(G_j) for a real V
 __global__ void k_mu(int n, int n_w, int j0, int M2, int L, int n_chunks, const double2 *part,
-                     const double2 *coef, double2 *mu, int accumulate) {
+                     const double2 *coef, double2 *mu, int accumulate, int mirror) {
   const int e = blockIdx.y, k = blockIdx.x;
   const int LL = L * L;
   for (int pidx = threadIdx.x; pidx < LL; pidx += blockDim.x) {
@@ -152,6 +168,13 @@ __global__ void k_mu(int n, int n_w, int j0, int M2, int L, int n_chunks, const 
       const double2 b = coef[((int64_t)(j0 + jj) * 2 + 1) * M2 + k];
       acc = cfma(a, g, acc);
       acc = cfma(make_double2(-b.x, -b.y), gd, acc);
+      if (mirror > 0) {
+        const int jm = mirror - 1 - j0 - jj;
+        const double2 am = coef[((int64_t)jm * 2 + 0) * M2 + k];
+        const double2 bm = coef[((int64_t)jm * 2 + 1) * M2 + k];
+        acc = cfma(am, cconj(g), acc);
+        acc = cfma(make_double2(-bm.x, -bm.y), cconj(gd), acc);
+      }
     }
     *out = acc;
   }
@@ -166,7 +189,7 @@ int vhy_chunks(int64_t N) {
 
 cbs_status launch_mu(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, const double2 *V,
                      const double2 *Y, const double2 *coef, double2 *part, double2 *mu,
-                     bool accumulate, cudaStream_t st) {
+                     bool accumulate, int mirror, cudaStream_t st) {
   if (L > 64) {
     set_error("L must be <= 64 for the moment kernel");
     return CBS_EINVAL;
@@ -180,7 +203,7 @@ cbs_status launch_mu(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, c
   cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   k_mu<<<dim3((unsigned)(2 * M), (unsigned)n_e, 1), 256, 0, st>>>(n, n_w, j0, 2 * M, L, nch, part,
-                                                                 coef, mu, accumulate ? 1 : 0);
+                                                                 coef, mu, accumulate ? 1 : 0, mirror);
   cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   return CBS_OK;

@@ -83,18 +83,24 @@ __global__ void k_expand_systems(int n_e, int n_int, const double2 *z1, const do
   }
 }
 
-// Sets *bad when any of the count complex entries of A is not finite.
+// *flags |= 1 when any of the count complex entries of A is not finite, |= 2 when any has a
+// non-zero imaginary part.
 __global__ void k_nonfinite(int64_t count, const double2 *A, int *bad) {
   int b = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
     b |= !(isfinite(A[i].x) && isfinite(A[i].y));
-  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
+    b |= (A[i].y != 0.0) << 1;
+  }
+  const int f = (__syncthreads_or(b & 1) ? 1 : 0) | (__syncthreads_or(b & 2) ? 2 : 0);
+  if (f && threadIdx.x == 0) atomicOr(bad, f);
 }
 
 // Host-side check of a right-hand-side block on the device: CBS_EINVAL with a message
 // when it holds a NaN or an infinity (BiCG on such a block would only spread it).
-static cbs_status check_finite_block(int64_t count, const double2 *A, const char *who, cudaStream_t st) {
+// *is_real (may be NULL) tells whether every entry is real.
+static cbs_status check_finite_block(int64_t count, const double2 *A, const char *who, cudaStream_t st,
+                                     bool *is_real = nullptr) {
   DevBuf flag;
   CBS_TRY(flag.alloc(sizeof(int)));
   CBS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
@@ -104,10 +110,11 @@ static cbs_status check_finite_block(int64_t count, const double2 *A, const char
   int bad = 0;
   CBS_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CBS_CUDA(cudaStreamSynchronize(st));
-  if (bad) {
+  if (bad & 1) {
     set_error(std::string(who) + ": the right-hand sides contain a NaN or an infinity");
     return CBS_EINVAL;
   }
+  if (is_real) *is_real = !(bad & 2);
   return CBS_OK;
 }
 
@@ -272,14 +279,13 @@ struct ShiftedSolver {
   static size_t bytes_per_system(const HamView &H, int L, int precision) {
     const size_t v16 = (size_t)H.n * L * 16;
     if (precision == CBS_FP64) return 2 * (4 * v16 + v16) + 2 * v16;   // state + residual check
-    if (precision == CBS_FP64_APPLY32) return 2 * (4 * v16 + v16) + 2 * v16 + 2 * v16;   // + complex64 p, q
     return 2 * (4 * v16 / 2) + 2 * v16 + 2 * v16 + 2 * v16;             // f32 state, Y, R, D
   }
   // device bytes per energy of a shifted family of n_pt points: scaled directions and
   // solutions of its 2 n_pt systems, plus the FP64 solutions kept for the moments
   static size_t family_bytes_per_energy(const HamView &H, int n_pt, int L, int precision) {
     const size_t v16 = (size_t)H.n * L * 16;
-    const bool fp64 = precision != CBS_FP32_REFINE;
+    const bool fp64 = precision == CBS_FP64;
     const size_t vr = fp64 ? v16 : v16 / 2;
     return (size_t)2 * n_pt * (2 * vr + (fp64 ? 0 : v16));
   }
@@ -312,8 +318,7 @@ struct ShiftedSolver {
     CBS_TRY(rc.alloc(H, n, L));
     rc.profile = o.profile != 0;
     b64.profile = b32.profile = o.profile != 0;
-    if (o.precision != CBS_FP32_REFINE) {
-      b64.apply32 = o.precision == CBS_FP64_APPLY32;
+    if (o.precision == CBS_FP64) {
       CBS_TRY(b64.alloc(H, n, L));
       if (group > 0 && o.stop_fraction < 1.0) {
         b64.group = group;
@@ -323,20 +328,6 @@ struct ShiftedSolver {
       CBS_TRY(b64.init(B, 0, B, 0, nullptr, o.tol, 0.0, st));
       int done = 0;
       CBS_TRY(b64.iterate(o.tol, o.max_iter, o.check_every, st, &done));
-      if (o.precision == CBS_FP64_APPLY32) {
-        // the recursion ran on a complex64 operator: keep its solution and continue the
-        // columns whose FP64 true residual misses tol
-        CBS_TRY(ybuf.alloc((size_t)2 * n * H.n * L * sizeof(double2)));
-        Y = ybuf.as<double2>();
-        CBS_CUDA(cudaMemcpyAsync(Y, b64.x, (size_t)2 * n * H.n * L * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-        CBS_CUDA(cudaMemcpyAsync(iters.data(), b64.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CBS_CUDA(cudaMemcpyAsync(flags.data(), b64.flags, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CBS_CUDA(cudaStreamSynchronize(st));
-        for (auto &f : flags) f &= 2 | 64;
-        CBS_TRY(collect_profile(st));
-        b64.release();
-        return refine(o, st);
-      }
       Y = b64.x;
       CBS_TRY(rc.run(H, Y, B, b64.tw, b64.E, o.tol, st, nullptr));
       CBS_CUDA(cudaMemcpyAsync(iters.data(), b64.iters, (size_t)n * L * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -424,10 +415,7 @@ struct ShiftedSolver {
     }
     if (unconv > 0) {
       // FP64 BiCG for the columns left: P(z) D = R, P(z)^dagger D~ = R~ to tol relative to
-      // the original right-hand side, then Y += D (operator in complex64 with
-      // CBS_FP64_APPLY32: the continuation starts from a residual ~1e-6 of the original, and
-      // a complex64 apply reaches ~1e-7 of that)
-      b64.apply32 = o.precision == CBS_FP64_APPLY32;
+      // the original right-hand side, then Y += D
       CBS_TRY(b64.alloc(H, n, L));
       CBS_TRY(b64.set_systems(zs, Es, st));
       CBS_TRY(b64.init(rc.R, (int64_t)H.n * L, rc.R + (size_t)n * H.n * L, (int64_t)H.n * L,
@@ -474,7 +462,6 @@ struct ShiftedSolver {
     for (int e = 0; e < n_e; ++e) sig[e] = energies_h[e] - E0;
     const bool mixed = sizeof(R) == sizeof(float);
     const double ftol = mixed ? std::max(o.tol, o.family_tol > 0 ? o.family_tol : 1e-6) : o.tol;
-    fam.seed.apply32 = o.precision == CBS_FP64_APPLY32;
     CBS_TRY(fam.alloc(H, n_pt, n_e, L));
     fam.group_need = stop_need(o, n_pt);
     CBS_TRY(fam.init(z1, E0, sig.data(), B, ftol, st));
@@ -557,11 +544,12 @@ static cbs_status check_opts(const cbs_options *opt, cbs_options *o) {
   if (opt) *o = *opt;
   else cbs_options_default(o);
   if (!(o->tol > 0) || !(o->delta > 0) || !(o->rho_max > 0) || o->max_iter < 1 ||
-      (o->precision != CBS_FP64 && o->precision != CBS_FP32_REFINE && o->precision != CBS_FP64_APPLY32) ||
+      (o->precision != CBS_FP64 && o->precision != CBS_FP32_REFINE) ||
       (o->extraction != CBS_HANKEL && o->extraction != CBS_RR) || !(o->inner_tol > 0) ||
       o->max_sweeps < 0 || o->inner_max_iter < 1 || o->stall_sweeps < 1 ||
       (o->multi_shift != 0 && o->multi_shift != 1) || o->family_tol < 0 || o->family_tol >= 1 ||
-      !(o->stop_fraction > 0 && o->stop_fraction <= 1.0) || o->points_per_wave < 0) {
+      !(o->stop_fraction > 0 && o->stop_fraction <= 1.0) || o->points_per_wave < 0 ||
+      (o->conj_points != 0 && o->conj_points != 1)) {
     set_error("invalid cbs_options");
     return CBS_EINVAL;
   }
@@ -635,7 +623,14 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
   CBS_TRY(vbuf.alloc((size_t)N * L * sizeof(double2)));
   double2 *dV = vbuf.as<double2>();
   CBS_CUDA(cudaMemcpyAsync(dV, V, (size_t)N * L * sizeof(double2), cudaMemcpyDefault, st));
-  CBS_TRY(check_finite_block((int64_t)N * L, dV, "cbs_solve", st));
+  bool v_real = false;
+  CBS_TRY(check_finite_block((int64_t)N * L, dV, "cbs_solve", st, &v_real));
+  // Conjugate points (§3.2 contour, real blocks H0, H+, H- and real E): the outer-circle points
+  // come in pairs z_{n_int-1-j} = conj(z_j) (theta -> 2 pi - theta), and so do their dual
+  // twists; P(conj z) = conj(P(z)), so with a real V the solutions there are conj(Y_j) and
+  // conj(Y~_j).  Only the first n_int/2 points are solved; the moments add the conjugates.
+  const bool mirror = o.conj_points && v_real && n_int % 2 == 0;
+  const int n_solve = mirror ? n_int / 2 : n_int;
   // contour
   DevBuf cbuf;
   CBS_TRY(cbuf.alloc((size_t)n_int * (4 * M + 1) * sizeof(double2) + (size_t)n_e * sizeof(double) + 512));
@@ -661,7 +656,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
     const size_t pairs = ne_ * nw_;
     size_t solve;
     if (o.multi_shift) {
-      const size_t vr = o.precision != CBS_FP32_REFINE ? v16 : v16 / 2;
+      const size_t vr = o.precision == CBS_FP64 ? v16 : v16 / 2;
       const size_t fam = pairs * ShiftedSolver::family_bytes_per_energy(H, 1, L, o.precision) +
                          nw_ * (2 * 4 * vr + dsz);                        // + seed per point
       const size_t ref = pairs * 2 * v16 + nw_ * (per_sys + 2 * v16);   // Y + one energy's refinement
@@ -672,9 +667,9 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
     return solve + ne_ * extract_e + 2 * pairs * 8 * L * L * 16;
   };
   const size_t usable = free_b * 6 / 10;
-  int nb = 0, nw = n_int;
+  int nb = 0, nw = n_solve;
   if (o.energies_per_batch > 0) nb = std::min(o.energies_per_batch, n_e);
-  if (o.points_per_wave > 0) nw = std::min(o.points_per_wave, n_int);
+  if (o.points_per_wave > 0) nw = std::min(o.points_per_wave, n_solve);
   if (nb == 0) {
     for (int t = n_e; t >= 1; --t)
       if (peak(t, nw) <= usable) { nb = t; break; }
@@ -709,8 +704,8 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
     double2 *Sm = mbuf.as<double2>();
     double2 *mu = (double2 *)((char *)Sm + ((s_bytes + 255) & ~(size_t)255));
     double2 *part = (double2 *)((char *)mu + ((mu_bytes + 255) & ~(size_t)255));
-    for (int j0 = 0; j0 < n_int; j0 += nw) {
-      const int nwv = std::min(nw, n_int - j0);
+    for (int j0 = 0; j0 < n_solve; j0 += nw) {
+      const int nwv = std::min(nw, n_solve - j0);
       const int nsys = ne * nwv;
       DevBuf sysb;
       CBS_TRY(sysb.alloc((size_t)nsys * (sizeof(double2) + sizeof(double)) + 256));
@@ -721,7 +716,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
       // ---- step 1: shifted solves of this wave's points
       ShiftedSolver S;
       S.group = nwv;
-      if (o.multi_shift && o.precision != CBS_FP32_REFINE)
+      if (o.multi_shift && o.precision == CBS_FP64)
         CBS_TRY(S.run_family(S.ms, H, ne, nwv, L, z1 + j0, energies + e0, zs, Es, dV, o, st));
       else if (o.multi_shift)
         CBS_TRY(S.run_family(S.ms32, H, ne, nwv, L, z1 + j0, energies + e0, zs, Es, dV, o, st));
@@ -740,13 +735,19 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
             b_iters[dst] = S.iters[src];
             b_flags[dst] = S.flags[src];
             b_maxrel[dst] = S.maxrel[src];
+            if (mirror) {      // the conjugate point's solve is this one's conjugate
+              const size_t dm = ((size_t)e * n_int + (n_int - 1 - j0 - jj)) * L + c;
+              b_iters[dm] = S.iters[src];
+              b_flags[dm] = S.flags[src];
+              b_maxrel[dm] = S.maxrel[src];
+            }
           }
       b_sweeps = std::max(b_sweeps, S.sweeps);
       b_fp64 = b_fp64 || S.fp64_continued;
       CBS_TRY(lap(&res->ms_solve));
       // ---- step 2: this wave's share of the moments
-      CBS_TRY(launch_moments(nsys, ne, nwv, j0, M, N, L, S.Y, coef, Sm, j0 > 0, st));
-      CBS_TRY(launch_mu(nsys, ne, nwv, j0, M, N, L, dV, S.Y, coef, part, mu, j0 > 0, st));
+      CBS_TRY(launch_moments(nsys, ne, nwv, j0, M, N, L, S.Y, coef, Sm, j0 > 0, mirror ? n_int : 0, st));
+      CBS_TRY(launch_mu(nsys, ne, nwv, j0, M, N, L, dV, S.Y, coef, part, mu, j0 > 0, mirror ? n_int : 0, st));
       CBS_TRY(lap(&res->ms_moments));
     }
     // ---- step 3: extraction (Hankel SVD, reduced eigenproblem, vectors, residuals)

@@ -15,8 +15,9 @@ a seeded stand-in with the paper's structure:
 * separable non-local projectors per atom: a Gaussian radial part times real
   spherical harmonics with l <= 1 (s, p_x, p_y, p_z), hard cut at ``r_c``,
   discretely normalised, with a diagonal coupling block ``h_a``,
-* the block ``V`` of right-hand sides: i.i.d. complex Gaussians (real and imaginary
-  parts N(0, 1)).
+* the block ``V`` of right-hand sides: i.i.d. real Gaussians N(0, 1).  The blocks of the
+  Hamiltonian are real, so with a real ``V`` the solutions at conjugate contour points are
+  complex conjugates of each other, which the library uses to solve half the points.
 
 Projector table format (consumed as-is by both sides):
 
@@ -39,7 +40,7 @@ import numpy as np
 
 __all__ = [
     "Grid", "Projectors", "Workload",
-    "gaussian_wells", "make_projectors", "random_rhs",
+    "gaussian_wells", "make_projectors", "random_rhs", "random_rhs_complex",
     "workload", "tiny_workload", "CONFIG_NAMES",
 ]
 
@@ -186,11 +187,15 @@ def make_projectors(g: Grid, centres: np.ndarray, r_c: float = 2.0, sigma: float
 
 
 def random_rhs(n: int, L: int, seed: int) -> np.ndarray:
-    """Block of L complex Gaussian right-hand sides, real and imaginary parts N(0,1)."""
+    """Block of L real Gaussian right-hand sides, entries N(0,1), stored as complex128."""
     rng = np.random.default_rng([seed, 0x5EED])
-    re = rng.standard_normal((n, L))
-    im = rng.standard_normal((n, L))
-    return re + 1j * im
+    return rng.standard_normal((n, L)).astype(np.complex128)
+
+
+def random_rhs_complex(n: int, L: int, seed: int) -> np.ndarray:
+    """Block of L complex Gaussian right-hand sides, real and imaginary parts N(0,1)."""
+    rng = np.random.default_rng([seed, 0xC0DE])
+    return rng.standard_normal((n, L)) + 1j * rng.standard_normal((n, L))
 
 
 CONFIG_NAMES = ("c1", "c2", "c3", "c4a", "c4b", "c4c", "c5")
