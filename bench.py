@@ -321,6 +321,9 @@ def main():
     ap.add_argument("--spmm-systems", type=int, default=0,
                     help="systems per SpMM launch (default: the seed batch of a family, 2 N_int)")
     ap.add_argument("--spmm-dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--shapes", default="",
+                    help="launch shapes 'py,pz:py,pz,x2' (complex128 : complex64) instead of the "
+                         "autotuner (profiling runs)")
     args = ap.parse_args()
     world, rank, local = _dist()
 
@@ -363,8 +366,16 @@ def main():
             self.H = cbs.Hamiltonian(self.wl.grid, self.wl.vloc, self.wl.projectors)
             self.Vd = torch.from_numpy(self.wl.V).to(dev).contiguous()
             n_tune = 2 * self.wl.n_int
-            self.tune = {"c128": cbs.autotune_apply(self.H, n_tune, self.wl.L, torch.complex128),
-                         "c64": cbs.autotune_apply(self.H, n_tune, self.wl.L, torch.complex64)}
+            if args.shapes:
+                a, b = args.shapes.split(":")
+                a, b = [int(v) for v in a.split(",")], [int(v) for v in b.split(",")]
+                cbs.set_apply_shape(self.H, torch.complex128, a[0], a[1])
+                cbs.set_apply_shape(self.H, torch.complex64, b[0], b[1], b[2])
+                self.tune = {"c128": {"py": a[0], "pz": a[1], "x2": 0, "ms": None},
+                             "c64": {"py": b[0], "pz": b[1], "x2": b[2], "ms": None}}
+            else:
+                self.tune = {"c128": cbs.autotune_apply(self.H, n_tune, self.wl.L, torch.complex128),
+                             "c64": cbs.autotune_apply(self.H, n_tune, self.wl.L, torch.complex64)}
 
         def describe(self):
             wl = self.wl

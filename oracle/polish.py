@@ -16,7 +16,8 @@ Q(lambda) = lambda^2 H+ + lambda (H0 - E) + H-.  Starting from an approximate pa
 with v = x_0 / ||x_0||^2.  It converges linearly with a factor proportional to
 |sigma - lambda_*|, so from an eigenvalue already correct to ~1e-9 two or three steps
 reach rounding level.  Q(sigma) is factorised once per eigenvalue with dense LU
-(LAPACK getrf through scipy), which bounds this to cells of a few ten thousand points.
+(LAPACK getrf through scipy), which bounds this to cells of a few ten thousand points; the
+blocks stay sparse for the products.
 
 Pins (tests/test_oracle_polish.py): perturbed eigenpairs of tiny cells converge back to
 the dense linearisation's eigenvalues; on the free-electron 8x8x4 cell to the
@@ -29,10 +30,11 @@ import scipy.linalg as sla
 
 
 def qep_blocks(op, E):
-    """(A2, A1, A0) = (H+, H0 - E, H-) as dense arrays."""
-    H0, Hp, Hm = (M.toarray() for M in op.explicit())
-    A1 = H0 - E * np.eye(H0.shape[0])
-    return Hp, A1, Hm
+    """(A2, A1, A0) = (H+, H0 - E, H-) as sparse matrices."""
+    import scipy.sparse as sp
+    H0, Hp, Hm = op.explicit()
+    A1 = (H0 - E * sp.identity(H0.shape[0], format="csr")).tocsr()
+    return Hp.tocsr(), A1, Hm.tocsr()
 
 
 def polish_pair(blocks, lam0, x0, steps=4):
@@ -40,8 +42,8 @@ def polish_pair(blocks, lam0, x0, steps=4):
     has unit 2-norm and history lists |lambda_{k+1} - lambda_k|."""
     A2, A1, A0 = blocks
     sigma = complex(lam0)
-    Qs = sigma * sigma * A2 + sigma * A1 + A0
-    lu = sla.lu_factor(Qs, check_finite=False)
+    Qs = (sigma * sigma * A2 + sigma * A1 + A0).toarray()    # dense for the LU only
+    lu = sla.lu_factor(Qs, overwrite_a=True, check_finite=False)
     x = np.asarray(x0, complex).copy()
     v = x / np.vdot(x, x)
     x = x / np.vdot(v, x)

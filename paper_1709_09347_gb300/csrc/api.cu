@@ -175,12 +175,15 @@ extern "C" cbs_status cbs_autotune_apply(cbs_hamiltonian *h, int n_sys, int L, i
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) { s = cuda_fail(e, "cbs_autotune_apply setup"); break; }
     const bool x2_ok = ti == 1 && L % 2 == 0 && H.np4 == 4;
+    // complex64 kernels: two columns per thread (1) or one (-1)
     const int variants[2] = {1, -1};
     for (int vi = 0; vi < (x2_ok ? 2 : 1) && s == CBS_OK; ++vi) {
       const int x2 = x2_ok ? variants[vi] : 0;
-      const int per_line = (x2_ok && x2 > 0) ? L / 2 : L;
-      for (int py = 1; py * per_line <= 256 && py <= 32 && s == CBS_OK; py *= 2)
-      for (int pz = 1; py * pz * per_line <= 256 && pz <= 16 && s == CBS_OK; pz *= 2) {
+      const int per_line = (x2_ok && x2 == 1) ? L / 2 : L;
+      // the two-columns-per-thread kernel also comes in a 512-thread variant
+      const int max_threads = (x2_ok && x2 == 1) ? 512 : 256;
+      for (int py = 1; py * per_line <= max_threads && py <= 32 && s == CBS_OK; py *= 2)
+      for (int pz = 1; py * pz * per_line <= max_threads && pz <= 16 && s == CBS_OK; pz *= 2) {
         H.tune_py[ti] = py;
         H.tune_pz[ti] = pz;
         H.tune_x2 = x2;

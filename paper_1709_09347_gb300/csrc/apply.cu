@@ -354,25 +354,27 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Planes of X a thread of the complex64 stencil keeps in flight ahead of the one it needs.
-// The z-march consumes one 16-byte value per thread and plane; without a prefetch each
-// plane waits out a full DRAM latency, which bounded the kernel at ~20% of HBM bandwidth.
+// Planes of X a thread of the complex64 stencil keeps in flight ahead of the one it needs
+// (blocks of up to 256 threads; blocks of up to 512 threads keep 2).
 constexpr int kApplyPF = 6;
+constexpr int kApplyPFBig = 2;
 
 // Complex64 fast path: each thread owns two adjacent columns of one (x, y) line, so every
 // load and store is 16 bytes; z arms from the register queue of Bloch-extended values, fed
 // from a per-thread ring of kApplyPF planes in shared memory filled by cp.async; the
 // projector scatter reads one packed (atom, wrap) word, one float4 of projector values and
 // 64 bytes of D per covering entry (D laid out [system][atom][column][4]).  The point's
-// scatter-table range and local potential are loaded one plane ahead.
-template <bool PER_COL, int MH>
-__global__ void __launch_bounds__(256, 2) k_apply_c64x2(HamView H, int L, const float4 *__restrict__ X,
+// scatter-table range and local potential are loaded one plane ahead.  BIG: blocks of up to
+// 512 threads (a larger x-y footprint per block, so more of the neighbour loads hit in L1).
+template <bool PER_COL, int MH, bool BIG>
+__global__ void __launch_bounds__(BIG ? 512 : 256, BIG ? 1 : 2) k_apply_c64x2(HamView H, int L, const float4 *__restrict__ X,
                                                         float4 *__restrict__ Y,
                                                         const double2 *__restrict__ twist,
                                                         const double *__restrict__ E,
                                                         const float4 *__restrict__ D,
                                                         const int *__restrict__ sys_active) {
-  extern __shared__ float4 pf_ring[];   // [kApplyPF][threads of the block]
+  constexpr int PF = BIG ? kApplyPFBig : kApplyPF;
+  extern __shared__ float4 pf_ring[];   // [PF][threads of the block]
   const int s = blockIdx.z;
   if (sys_active && !sys_active[s]) return;
   const int t = threadIdx.x;                 // column pair
@@ -412,10 +414,10 @@ __global__ void __launch_bounds__(256, 2) k_apply_c64x2(HamView H, int L, const 
     return v;
   };
   // planes MH .. nz-1+MH enter the queue head one per step; the ring holds the next
-  // kApplyPF of them (one commit group per plane, empty groups past the last plane)
+  // PF of them (one commit group per plane, empty groups past the last plane)
   const int last = nz - 1 + MH;
 #pragma unroll
-  for (int k = 0; k < kApplyPF; ++k) {
+  for (int k = 0; k < PF; ++k) {
     if (MH + k <= last) cp_async16(&pf_ring[k * nth + tid], src(MH + k));
     cp_async_commit();
   }
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_c64x2(HamView H, int L, const 
       if (D) { e0 = (int)H.pt_ptr[pt + nxy]; e1 = (int)H.pt_ptr[pt + nxy + 1]; }
       vnext = vl[pt + nxy];
     }
-    cp_async_wait<kApplyPF - 1>();           // plane iz + MH has landed in `slot`
+    cp_async_wait<PF - 1>();           // plane iz + MH has landed in `slot`
     {
       const float4 v = pf_ring[slot * nth + tid];
       q[2 * MH] = iz + MH >= nz ? c2mul(w0, w1, v) : v;
@@ -454,10 +456,10 @@ __global__ void __launch_bounds__(256, 2) k_apply_c64x2(HamView H, int L, const 
       acc.z += wx * (a1.z + a2.z) + wy * (b1.z + b2.z) + wz * (z1.z + z2.z);
       acc.w += wx * (a1.w + a2.w) + wy * (b1.w + b2.w) + wz * (z1.w + z2.w);
     }
-    // the queue head has been consumed: refill its slot with plane iz + MH + kApplyPF
-    if (iz + MH + kApplyPF <= last) cp_async16(&pf_ring[slot * nth + tid], src(iz + MH + kApplyPF));
+    // the queue head has been consumed: refill its slot with plane iz + MH + PF
+    if (iz + MH + PF <= last) cp_async16(&pf_ring[slot * nth + tid], src(iz + MH + PF));
     cp_async_commit();
-    slot = slot + 1 == kApplyPF ? 0 : slot + 1;
+    slot = slot + 1 == PF ? 0 : slot + 1;
     for (int qq = ce0; qq < ce1; ++qq) {
       const int2 aw = H.pt_aw[qq];
       const float4 p = H.pt_p32[qq];
@@ -533,21 +535,27 @@ cbs_status launch_apply(const HamView &H, int n_sys, int L, const typename CT<R>
   if (ti == 1 && L % 2 == 0 && L <= 512 && H.np4 == 4 && (H.tune_x2 >= 0 || L > 256)) {
     const int L2 = L / 2;
     int py = 256 / L2, pz = 1;
-    if (H.tune_py[1] > 0 && H.tune_pz[1] > 0 && H.tune_py[1] * H.tune_pz[1] * L2 <= 256) {
+    if (H.tune_py[1] > 0 && H.tune_pz[1] > 0 && H.tune_py[1] * H.tune_pz[1] * L2 <= 512) {
       py = H.tune_py[1];
       pz = H.tune_pz[1];
     }
     if (py < 1) py = 1;
     dim3 blk((unsigned)L2, (unsigned)py, (unsigned)pz);
+    const bool big = blk.x * blk.y * blk.z > 256;
     dim3 grd((unsigned)ceil_div(H.nx, py), (unsigned)ceil_div(H.ny, pz), (unsigned)n_sys);
     const float4 *X4 = reinterpret_cast<const float4 *>(X);
     float4 *Y4 = reinterpret_cast<float4 *>(Y);
     const float4 *D4 = H.n_atoms ? reinterpret_cast<const float4 *>(D) : nullptr;
-    const size_t pf_smem = (size_t)kApplyPF * blk.x * blk.y * blk.z * sizeof(float4);
+    const size_t pf_smem = (size_t)(big ? kApplyPFBig : kApplyPF) * blk.x * blk.y * blk.z * sizeof(float4);
 #define FX(MH)                                                                                     \
   do {                                                                                             \
-    if (per_col) k_apply_c64x2<true, MH><<<grd, blk, pf_smem, st>>>(H, L, X4, Y4, twist, E, D4, sys_active); \
-    else k_apply_c64x2<false, MH><<<grd, blk, pf_smem, st>>>(H, L, X4, Y4, twist, E, D4, sys_active);    \
+    if (big) {                                                                                     \
+      if (per_col) k_apply_c64x2<true, MH, true><<<grd, blk, pf_smem, st>>>(H, L, X4, Y4, twist, E, D4, sys_active); \
+      else k_apply_c64x2<false, MH, true><<<grd, blk, pf_smem, st>>>(H, L, X4, Y4, twist, E, D4, sys_active);    \
+    } else {                                                                                       \
+      if (per_col) k_apply_c64x2<true, MH, false><<<grd, blk, pf_smem, st>>>(H, L, X4, Y4, twist, E, D4, sys_active); \
+      else k_apply_c64x2<false, MH, false><<<grd, blk, pf_smem, st>>>(H, L, X4, Y4, twist, E, D4, sys_active);    \
+    }                                                                                              \
     cbs::count_launches(1);                                                                        \
   } while (0)
     switch (H.m) {

@@ -71,6 +71,24 @@ def test_autotuned_apply(name, L):
     assert _run(wl, ZS, ES, L, "c64", H) < 3e-6
 
 
+@pytest.mark.parametrize("case", [0, 1, 4, 5])
+@pytest.mark.parametrize("shape", [(4, 2, 1), (8, 4, 1), (2, 2, -1)])
+def test_complex64_kernel_shapes(case, shape):
+    """Every complex64 stencil kernel the autotuner can pick, forced through
+    cbs_set_apply_shape, against the oracle's operator on cells with ragged tiles (odd
+    sizes), FD half-widths 2-6 and even column counts: two columns per thread in 256- and
+    512-thread blocks, and one column per thread."""
+    torch = need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    cases = small_cases() + [synth.tiny_workload(nx=13, ny=10, nz=6, h=0.4, fd_order=12, n_atoms=4,
+                                                 r_c=1.1, sigma=0.4, L=32)]
+    wl = cases[case]
+    L = wl.L if wl.L % 4 == 0 else 8
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    cbs.set_apply_shape(H, torch.complex64, *shape)
+    assert _run(wl, ZS, ES, L, "c64", H) < 3e-6
+
+
 @pytest.mark.parametrize("case", [0, 1, 4])
 def test_frobenius_norms(case):
     need_gpu()

@@ -122,46 +122,76 @@ def _conj_defect(lam):
     return np.array([np.min(np.abs(lam - np.conj(x))) for x in lam])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
-def test_solve_c2_vs_oracle_golden(precision):
-    """Full 32x32x16 cell (8th-order FD, 40 atoms x 4 projectors) at two energies against
-    stored oracle results (tests/golden/make_c2_oracle.py runs only the CPU oracle):
-    same eigenvalue count in the ring, eigenvalues within lam_tol, rank within 5%, and
-    every kept pair's residual recomputed with the oracle's operator <= 1e-8.
-
-    lam_tol: the oracle's own eigenvalues break conjugate symmetry by up to 8.6e-10 at the
-    second energy (the extraction amplifies the 1e-12 solve error), so both sides carry
-    errors of that size; two such approximations agree within 2e-9.  The mixed form stops
-    at the same tolerance by a different Krylov path and columns continued in FP64, so its
-    solve error within that tolerance differs: its bar is the rho_max = 1e-8 of the pair
-    filter (measured worst: 5e-9)."""
-    lam_tol = 2e-9 if precision == "fp64" else 1e-8
+def _c2_golden():
     import os
     g = np.load(os.path.join(os.path.dirname(__file__), "golden", "c2_oracle.npz"))
-    wl = synth.workload("c2")
-    idx = [int(i) for i in g["energy_index"]]
-    res = _gpu_solve(wl, wl.energies[idx], precision, tol=float(g["tol"]))
+    return g, [int(i) for i in g["energy_index"]]
+
+
+# The eigenvalue bar of the FP64 form against the stored energies' eigenvalues refined to
+# rounding level: 1e-10 relative.  Measured: the Rayleigh-Ritz extraction reaches 3.5e-13 with
+# BiCG tol 1e-12; the Hankel extraction of Algorithm 1 is limited by its own approximation to
+# 1.5e-10 (per energy) and 3.9e-10 (shifted family) at tol 1e-12 -- the oracle's own run is at
+# 2.5e-10 -- and reaches 1.7e-11 at tol 1e-13.
+C2_EXACT_TOL = 1e-10
+
+
+def _check_c2_golden(res, g, idx, lam_tol, wl, rank_mode):
+    """rank_mode: 'same_tol' (Hankel rank within 5% of the oracle's, solved to the same tol),
+    'bound' (rank >= the number of pairs: the delta cut moves with the solve error), or
+    'basis' (Rayleigh-Ritz: the reported rank is the basis size)."""
     op = CellOperator(wl.grid, wl.vloc, wl.projectors)
     for e, i in enumerate(idx):
         r = res.energies[e]
-        ref_lam = g[f"lam_{i}"]
-        assert len(r["lam"]) == len(ref_lam)
-        worst, un_f, un_r = match(r["lam"], ref_lam, lam_tol)
-        assert not un_f and not un_r and worst <= lam_tol
-        assert np.max(_conj_defect(r["lam"])) <= lam_tol
-        # the cut delta*sigma_1 falls in a continuum of leaked singular values whose size
-        # follows the solve error: in FP64 the count there may shift by a few percent; the
-        # mixed form's solve error (which columns stall and finish in FP64) moves it further,
-        # so there only the bound that holds for any correct solve is checked: every
-        # eigenvalue in the ring needs its own dimension
-        if precision == "fp64":
+        ref = g[f"lam_{i}"]                     # the oracle's Algorithm 1 at tol 1e-12
+        exact = g[f"lam_polished_{i}"]          # the same eigenvalues refined
+        assert len(r["lam"]) == len(ref)
+        if int(g[f"rank_{i}"]) == wl.L * wl.M and rank_mode != "basis":
+            assert r["rank"] == wl.L * wl.M and r["flags"] & 4   # saturation on both sides
+        elif rank_mode == "same_tol":
             assert abs(r["rank"] - int(g[f"rank_{i}"])) <= max(2, int(0.05 * int(g[f"rank_{i}"])))
         else:
-            assert r["rank"] >= len(ref_lam)
+            assert r["rank"] >= len(ref)
+        if not len(ref):
+            continue
+        worst, un_f, un_r = match(r["lam"], exact, lam_tol)
+        assert not un_f and not un_r and worst <= lam_tol
         E = float(wl.energies[i])
         rr = ss.residuals(op, E, r["lam"], r["vectors"], op.frobenius(E))
         assert np.all(rr <= 1e-8)
-        assert r["max_solve_residual"] <= 1e-9
+
+
+@pytest.mark.parametrize("form,tol,lam_tol,rank_mode", [
+    (dict(precision="fp64", extraction="rr"), 1e-12, C2_EXACT_TOL, "basis"),
+    (dict(precision="fp64", extraction="rr", multi_shift=1), 1e-12, C2_EXACT_TOL, "basis"),
+    (dict(precision="fp64"), 1e-13, C2_EXACT_TOL, "bound"),
+    (dict(precision="fp64", multi_shift=1), 1e-13, C2_EXACT_TOL, "bound"),
+    (dict(precision="fp64"), 1e-12, 5e-10, "same_tol"),
+    (dict(precision="fp32_refine"), 1e-12, 1e-8, "bound"),
+    (dict(precision="fp32_refine", multi_shift=1), 1e-12, 1e-8, "bound")])
+def test_solve_c2_vs_oracle_golden(form, tol, lam_tol, rank_mode):
+    """Full 32x32x16 cell (8th-order FD, 40 atoms x 4 projectors) at three stored energies
+    (tests/golden/make_c2_oracle.py runs only the CPU oracle; one of them rank-saturated):
+    the same eigenvalue count in the ring as the oracle's Algorithm 1, the rank (saturation
+    on both sides), every kept pair's residual recomputed with the oracle's operator <= 1e-8,
+    the solves' FP64 true residuals, and the eigenvalues against the oracle's eigenvalues
+    refined to rounding level: within 1e-10 in the FP64 form (Rayleigh-Ritz at tol 1e-12,
+    Algorithm 1's Hankel extraction at tol 1e-13), within 5e-10 for Algorithm 1 at the
+    oracle's own tol 1e-12 (its approximation error there, measured 1.5e-10 against the
+    oracle's 2.5e-10), and within the residual bar 1e-8 in the mixed forms."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    g, idx = _c2_golden()
+    wl = synth.workload("c2")
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    res = cbs.solve(H, wl.energies[idx], wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=tol, **form), allow=(cbs.CBS_OK, cbs.CBS_WRANK))
+    _check_c2_golden(res, g, idx, lam_tol, wl, rank_mode)
+    # the shifted family and the mixed forms refine every column to tol on the FP64 true
+    # residual; plain per-energy BiCG stops on the recursive one (within a factor 2 here)
+    refined = form.get("multi_shift") or form.get("precision") == "fp32_refine"
+    for e in res.energies:
+        assert e["max_solve_residual"] <= (1.0 if refined else 2.0) * tol
 
 
 def test_solve_rr_tiny_projectors():
@@ -222,34 +252,6 @@ def test_solve_multishift_tiny():
         for k in range(2 * wl.M):
             scale = np.max(np.abs(ref.mu[k]))
             assert np.max(np.abs(r["mu"][k] - ref.mu[k])) <= 100 * 1e-12 * (1 / wl.lambda_min) ** (k + 1) * scale
-
-
-def test_solve_multishift_c2_vs_oracle_golden():
-    """multi_shift = 1 on the 32x32x16 cell at the two stored energies (seed: the higher
-    one): the same bars as the per-energy FP64 form."""
-    import os
-    need_gpu()
-    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "c2_oracle.npz"))
-    wl = synth.workload("c2")
-    idx = [int(i) for i in g["energy_index"]]
-    from paper_1709_09347_gb300 import cbs
-    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
-    res = cbs.solve(H, wl.energies[idx], wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
-                    cbs.options(tol=float(g["tol"]), multi_shift=1))
-    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
-    lam_tol = 2e-9
-    for e, i in enumerate(idx):
-        r = res.energies[e]
-        ref_lam = g[f"lam_{i}"]
-        assert len(r["lam"]) == len(ref_lam)
-        worst, un_f, un_r = match(r["lam"], ref_lam, lam_tol)
-        assert not un_f and not un_r and worst <= lam_tol
-        assert np.max(_conj_defect(r["lam"])) <= lam_tol
-        assert abs(r["rank"] - int(g[f"rank_{i}"])) <= max(2, int(0.05 * int(g[f"rank_{i}"])))
-        E = float(wl.energies[i])
-        rr = ss.residuals(op, E, r["lam"], r["vectors"], op.frobenius(E))
-        assert np.all(rr <= 1e-8)
-        assert r["max_solve_residual"] <= 1e-9
 
 
 def test_solve_multishift_single_energy_and_rr():
@@ -315,13 +317,13 @@ def test_scan_batches_and_branches():
 
 def test_bench_configuration_properties():
     """The bench's own configuration: all 16 energies of the 32x32x16 cell, the paper's BiCG
-    tolerance 1e-10, shifted family.  What holds for any correct result: every kept pair's
-    residual, recomputed with the oracle's operator, is <= 1e-8 and equals the reported one;
-    each energy's kept set is closed under conjugation (real blocks; the eigenvalue error
-    scales with the solve tolerance, 8.6e-10 at 1e-12 in the stored oracle results, so 1e-6
-    here); at the two stored energies the counts equal the oracle's and the eigenvalues agree
-    within the same 1e-6."""
-    import os
+    tolerance 1e-10, FP64 shifted family, half the points (real V).  What holds for any
+    correct result: every solve's FP64 true residual <= tol; every kept pair's residual,
+    recomputed with the oracle's operator, is <= 1e-8 and equals the reported one; each
+    energy's kept set closed under conjugation; at the stored energies the counts and the
+    rank saturation equal the oracle's and the eigenvalues are within 1e-6 of the refined
+    ones (the accuracy the 1e-10 solves give the Hankel extraction, up to 1.4e-6 measured on
+    the 96x96x20 cell)."""
     need_gpu()
     from paper_1709_09347_gb300 import cbs
     wl = synth.workload("c2")
@@ -332,18 +334,16 @@ def test_bench_configuration_properties():
     assert len(res.energies) == len(wl.energies)
     for e, E in enumerate(wl.energies):
         r = res.energies[e]
+        assert r["max_solve_residual"] <= wl.tol
         if len(r["lam"]) == 0:
             continue
         rr = ss.residuals(op, float(E), r["lam"], r["vectors"], op.frobenius(float(E)))
         assert np.all(rr <= 1e-8)
-        assert np.allclose(rr, r["residual"], rtol=1e-6, atol=1e-15)
-        assert np.max(_conj_defect(r["lam"])) <= 1e-6
-    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "c2_oracle.npz"))
-    for i in (int(x) for x in g["energy_index"]):
-        ref = g[f"lam_{i}"]
-        assert len(res.energies[i]["lam"]) == len(ref)
-        worst, un_f, un_r = match(res.energies[i]["lam"], ref, 1e-6)
-        assert not un_f and not un_r
+        assert np.allclose(rr, r["residual"], rtol=1e-5, atol=1e-15)
+        assert np.max(_conj_defect(r["lam"]) / np.abs(r["lam"])) <= 1e-8
+    g, idx = _c2_golden()
+    sub = type("R", (), {"energies": [res.energies[i] for i in idx]})()
+    _check_c2_golden(sub, g, idx, 1e-6, wl, "bound")
 
 
 @pytest.mark.parametrize("multi_shift", [0, 1])
@@ -462,8 +462,8 @@ def test_solve_c3_inring_energy_properties():
     rr = ss.residuals(op, E, e["lam"], e["vectors"], op.frobenius(E))
     assert np.all(rr <= 1e-8)
     assert np.allclose(rr, e["residual"], rtol=1e-5, atol=1e-15)
-    assert np.max(_conj_defect(e["lam"]) / np.abs(e["lam"])) <= 1e-6
-    assert np.max(_closure_defect(e["lam"])) <= 1e-6
+    assert np.max(_conj_defect(e["lam"]) / np.abs(e["lam"])) <= 1e-8
+    assert np.max(_closure_defect(e["lam"])) <= 1e-5
     assert np.sum(np.abs(np.abs(e["lam"]) - 1.0) < 1e-6) >= 2
 
 
@@ -526,5 +526,38 @@ def test_solve_c4_cells_properties(name):
         rr = ss.residuals(op, E, e["lam"], e["vectors"], op.frobenius(E))
         assert np.all(rr <= 1e-8)
         assert np.allclose(rr, e["residual"], rtol=1e-5, atol=1e-15)
-        assert np.max(_conj_defect(e["lam"]) / np.abs(e["lam"])) <= 1e-6
-        assert np.max(_closure_defect(e["lam"])) <= 1e-6
+        # closure holds to the accuracy 1e-10 solves give the Hankel extraction (up to
+        # 1.4e-6 measured on the 96x96x20 cell); the conjugation closure holds to rounding for a real V
+        assert np.max(_conj_defect(e["lam"]) / np.abs(e["lam"])) <= 1e-8
+        assert np.max(_closure_defect(e["lam"])) <= 1e-5
+
+
+def test_c5_operator_and_waves():
+    """The nanotube-scale cell (160x160x32 = 819,200 points, h = 0.2, 640 atoms with 4
+    projectors, L = 48): the FP64 and complex64 applies against the oracle's operator on two
+    columns; and the whole method with the quadrature points streamed in waves (8 solved
+    points per wave, half the ring by the conjugate-point symmetry), cut at 20 BiCG
+    iterations: the call completes with CBS_ENOCONV, every point is accounted for in the
+    per-point statistics, and the accumulated moments are finite."""
+    torch = need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = synth.workload("c5")
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((1, op.n, 2)) + 1j * rng.standard_normal((1, op.n, 2))
+    z, E = 2.0 * np.exp(0.4j), 0.1
+    ref = op.apply_P(z, E, X[0])
+    for dt, bar in ((torch.complex128, 1e-13), (torch.complex64, 3e-6)):
+        Xd = torch.from_numpy(X).to("cuda").to(dt).contiguous()
+        Y = cbs.apply(H, [z], [E], Xd).to(torch.complex128).cpu().numpy()[0]
+        r = ref if dt == torch.complex128 else op.apply_P(z, E, Xd.to(torch.complex128).cpu().numpy()[0])
+        assert rel_err(Y, r) < bar
+    res = cbs.solve(H, wl.energies[3:4], wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
+                    cbs.options(tol=wl.tol, multi_shift=1, max_iter=20, points_per_wave=8),
+                    allow=(cbs.CBS_ENOCONV, cbs.CBS_WRANK))
+    e = res.energies[0]
+    assert res.status == cbs.CBS_ENOCONV and e["flags"] & 1
+    assert e["iters"].shape == (wl.n_int, wl.L)
+    assert np.all(e["iters"] >= 1) and np.array_equal(e["iters"], e["iters"][::-1])
+    assert np.all(np.isfinite(e["mu"]))
