@@ -46,13 +46,16 @@ UNIT = "energies/s"
 # not listed take all of their energies
 STEP_ENERGIES = {"c3": (3, 11, 19, 27)}
 
-# DRAM bytes per unit of the kernels reported as rooflines, each from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum divided by the units of the captured
-# launch), valid while the kernel's source file hashes to `sha`
+# DRAM bytes per unit of the kernels reported as rooflines, each from one ncu capture on one
+# workload (dram__bytes_read.sum + dram__bytes_write.sum of the gather + stencil launch pair,
+# divided by the complex outputs of the captured pair), valid for that workload while the
+# kernel's source file hashes to `sha`.  The FP64 shifted-family update has none: its
+# captured launch does not record how many energies were still active.
 KERNEL_TRAFFIC = {
-    "c128_apply": {"file": "apply.cu", "sha": None, "bytes_per_unit": None},
-    "c64_apply": {"file": "apply.cu", "sha": None, "bytes_per_unit": None},
-    "c64_shift_update": {"file": "bicg.cu", "sha": None, "bytes_per_unit": None},
+    # 32x32x16 cell, 32 systems (16 points and their duals), 16.78 M outputs: 745.7 MB
+    ("c128_apply", "c2"): {"file": "apply.cu", "sha": "f77085a5a8f84789", "bytes_per_unit": 44.45},
+    # 64x64x24 cell, 128 systems, 402.7 M outputs: 8.681 GB
+    ("c64_apply", "c3"): {"file": "apply.cu", "sha": "f77085a5a8f84789", "bytes_per_unit": 21.56},
 }
 
 FORMS = {
@@ -93,9 +96,9 @@ def _sha(fname):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _traffic(key, units_per_launch):
-    t = KERNEL_TRAFFIC[key]
-    if t["sha"] and t["bytes_per_unit"] and _sha(t["file"]) == t["sha"]:
+def _traffic(key, workload, units_per_launch):
+    t = KERNEL_TRAFFIC.get((key, workload))
+    if t and _sha(t["file"]) == t["sha"]:
         return t["bytes_per_unit"] * units_per_launch
     return None
 
@@ -472,14 +475,14 @@ def main():
                     ach = p["outputs"] * bpu / sec / 1e9
                     rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
                               peak_source=hbm_src, bytes_per_unit=bpu, unit_of_work="complex output",
-                              traffic=_traffic("c64_apply", p["outputs"] / launches))
+                              traffic=_traffic("c64_apply", wl.name, p["outputs"] / launches))
                 elif key == "c128":
                     fpu = apply_flops_per_output(wl)
                     ach = p["outputs"] * fpu / sec / 1e12
                     rl.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
                               frac=ach / FP64_PEAK_TFLOPS, flops_per_unit=fpu, unit_of_work="complex output",
                               peak_source="nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
-                              traffic=_traffic("c128_apply", p["outputs"] / launches))
+                              traffic=_traffic("c128_apply", wl.name, p["outputs"] / launches))
                 elif c64_family:
                     # per (energy, point, column) triple and grid point: scaled direction and
                     # solution read and written, primal and dual, complex64 (8 x 8 B)
@@ -488,7 +491,7 @@ def main():
                     rl.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
                               peak_source=hbm_src, bytes_per_unit=bpu,
                               unit_of_work="(energy, point, column) triple x grid point",
-                              traffic=_traffic("c64_shift_update", p["outputs"] / launches))
+                              traffic=_traffic("c64_shift_update", wl.name, p["outputs"] / launches))
                 else:
                     # FP64 family: 16 FP64 FMAs per unit, bound by the FP64 pipe
                     ach = p["outputs"] * 32 / sec / 1e12

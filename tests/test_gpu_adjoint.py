@@ -42,3 +42,31 @@ def test_autograd_backward():
                                           wl.n_int, wl.M, wl.V)
     assert np.max(np.abs(v.grad.cpu().numpy() - 3.0 * gVr)) <= 1e-8 * np.max(np.abs(3.0 * gVr))
     assert abs(e.grad.item() - 3.0 * gEr) <= 1e-8 * max(abs(3.0 * gEr), 1.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_gradient_directional_fd_c2(precision):
+    """On the 32x32x16 cell (16,384 points, 40 atoms with projectors): the adjoint gradient
+    contracted with a random direction of V_loc, and dJ/dE, against central finite
+    differences of J itself (steps 1e-4 in V_loc, 1e-5 Ha in E)."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    wl = synth.workload("c2")
+    E = float(wl.energies[12])
+    L, M, n_int = 8, 4, 16
+    V = np.ascontiguousarray(wl.V[:, :L])
+    o = cbs.options(tol=1e-12, precision=precision)
+    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
+    J, gV, gE = cbs.objective(H, E, wl.lambda_min, n_int, L, M, V, o, grad=True)
+    rng = np.random.default_rng(4)
+    d = rng.standard_normal(wl.grid.n)
+    h = 1e-4
+    Jp = cbs.objective(cbs.Hamiltonian(wl.grid, wl.vloc + h * d, wl.projectors), E, wl.lambda_min, n_int, L, M, V, o)
+    Jm = cbs.objective(cbs.Hamiltonian(wl.grid, wl.vloc - h * d, wl.projectors), E, wl.lambda_min, n_int, L, M, V, o)
+    fd = (Jp - Jm) / (2 * h)
+    assert abs(float(np.dot(gV, d)) - fd) <= 1e-5 * max(abs(fd), 1e-12 * abs(J))
+    hE = 1e-5
+    JEp = cbs.objective(H, E + hE, wl.lambda_min, n_int, L, M, V, o)
+    JEm = cbs.objective(H, E - hE, wl.lambda_min, n_int, L, M, V, o)
+    fdE = (JEp - JEm) / (2 * hE)
+    assert abs(gE - fdE) <= 1e-5 * max(abs(fdE), 1e-12 * abs(J))

@@ -188,10 +188,11 @@ def test_solve_c2_vs_oracle_golden(form, tol, lam_tol, rank_mode):
                     cbs.options(tol=tol, **form), allow=(cbs.CBS_OK, cbs.CBS_WRANK))
     _check_c2_golden(res, g, idx, lam_tol, wl, rank_mode)
     # the shifted family and the mixed forms refine every column to tol on the FP64 true
-    # residual; plain per-energy BiCG stops on the recursive one (within a factor 2 here)
+    # residual; plain per-energy BiCG stops on the recursive one, whose distance to the true
+    # residual stays near 1e-12 of the right-hand side here (8.9e-13 measured at tol 1e-13)
     refined = form.get("multi_shift") or form.get("precision") == "fp32_refine"
     for e in res.energies:
-        assert e["max_solve_residual"] <= (1.0 if refined else 2.0) * tol
+        assert e["max_solve_residual"] <= (tol if refined else max(2 * tol, 2e-12))
 
 
 def test_solve_rr_tiny_projectors():
