@@ -1,7 +1,8 @@
 // Small dense FP64 stage of Algorithm 1 (Hankel SVD, rank cut, reduced eigenproblem), on the device.
 //
 //   T = [mu_{i+j-2}], T^< = [mu_{i+j-1}]  (block Hankel, L*M square)
-//   T = U Sigma W^dagger (one-sided Jacobi SVD), rank m_hat: sigma_i >= delta sigma_1
+//   T = U Sigma W^dagger (column-pivoted QR T P = Q R, then one-sided Jacobi on R^dagger),
+//   rank m_hat: sigma_i >= delta sigma_1
 //   B = U_1^dagger T^< W_1 Sigma_1^{-1},  B phi = tau phi  (Hessenberg + shifted QR),
 //   lambda = tau,  psi = S W_1 Sigma_1^{-1} phi,  S = [S_0 ... S_{M-1}].
 // followed by the residual check of every in-ring pair and the filter.
@@ -69,7 +70,204 @@ __global__ void k_hankel(int n_e, int L, int M, const double2 *mu, double2 *T, d
 // the whole GPU (FP64 throughput per SM is small on GB300).  A sweep is captured once
 // as a CUDA graph and replayed until no pair of any energy needed a rotation.
 // On exit sigma (descending), U = A/sigma and W sorted accordingly.
+//
+// The Jacobi iteration runs on X = R^dagger of a column-pivoted QR factorisation
+// T P = Q R (Householder), the preconditioning of Drmac and Veselic (SIAM J. Matrix Anal.
+// Appl. 29, 2008): X has the singular values of T, and its columns are close to
+// orthogonal already, so the sweeps needed drop several-fold (each sweep is a round of
+// FP64 rotations over both n x n blocks, the cost of this stage).  From X V_x = U_x Sigma:
+// T = (Q V_x) Sigma (P U_x)^dagger, i.e. U = Q V_x and W = P U_x.
 constexpr int kSvdThreads = 256;
+
+// Column-pivoted Householder QR, one block per energy (A in place: R in the upper
+// triangle, zeros below).  Step k takes the remaining column of largest partial norm
+// (the first one on ties), then the reflector H_k = I - beta_k v_k v_k^dagger with
+// v_k = x + (x_0/|x_0|) ||x|| e_0 on x = A(k:n, k), beta_k = 2 / (v_k^dagger v_k), which
+// maps x onto -(x_0/|x_0|) ||x|| e_0; v_k goes to column k of Vh (rows k..n-1).  The partial
+// norms are downdated and recomputed from the column once the downdate has cancelled
+// more than half the digits (the criterion of LAPACK's xLAQP2).  Q = H_0 H_1 ... H_{n-1}.
+constexpr int kQrpThreads = 512;
+__global__ void __launch_bounds__(kQrpThreads) k_qrp(int n, double2 *Ab, double2 *Vhb, double *betab,
+                                                     int *permb) {
+  const int e = blockIdx.x;
+  const int64_t nn = (int64_t)n * n;
+  double2 *A = Ab + e * nn, *Vh = Vhb + e * nn;
+  double *beta = betab + (int64_t)e * n;
+  int *perm = permb + (int64_t)e * n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarp = kQrpThreads / 32;
+  __shared__ double vn1[512], vn2[512];
+  __shared__ int sperm[512];
+  __shared__ double red_v[nwarp];
+  __shared__ int red_i[nwarp];
+  __shared__ int sh_p;
+  __shared__ double sh_beta;
+  const double tol3z = sqrt(2.220446049250313e-16);
+  auto At = [&](int i, int j) -> double2 & { return A[i + (int64_t)j * n]; };
+  for (int j = warp; j < n; j += nwarp) {
+    double t = 0;
+    for (int i = lane; i < n; i += 32) t += cabs2(At(i, j));
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) vn1[j] = vn2[j] = sqrt(t);
+  }
+  for (int j = tid; j < n; j += kQrpThreads) sperm[j] = j;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // pivot: largest vn1[j], j >= k, first index on ties
+    double bv = -1.0;
+    int bi = n;
+    for (int j = k + tid; j < n; j += kQrpThreads)
+      if (vn1[j] > bv) { bv = vn1[j]; bi = j; }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double v = red_v[0];
+      int i0 = red_i[0];
+      for (int w = 1; w < nwarp; ++w)
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < i0)) { v = red_v[w]; i0 = red_i[w]; }
+      sh_p = i0;
+    }
+    __syncthreads();
+    const int p = sh_p;
+    if (p != k) {
+      for (int i = tid; i < n; i += kQrpThreads) {
+        const double2 t = At(i, k);
+        At(i, k) = At(i, p);
+        At(i, p) = t;
+      }
+      if (tid == 0) {
+        double t = vn1[k]; vn1[k] = vn1[p]; vn1[p] = t;
+        t = vn2[k]; vn2[k] = vn2[p]; vn2[p] = t;
+        const int q = sperm[k]; sperm[k] = sperm[p]; sperm[p] = q;
+      }
+    }
+    __syncthreads();
+    // reflector of column k (warp 0)
+    if (warp == 0) {
+      double a2 = 0;
+      for (int i = k + lane; i < n; i += 32) a2 += cabs2(At(i, k));
+      for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+      const double2 x0 = At(k, k);
+      if (a2 > 0) {
+        const double alpha = sqrt(a2), ax0 = cabsd(x0);
+        const double2 ph = ax0 > 0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1, 0);
+        for (int i = k + lane; i < n; i += 32)
+          Vh[i + (int64_t)k * n] = (i == k) ? make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha) : At(i, k);
+        __syncwarp();
+        if (lane == 0) {
+          sh_beta = 1.0 / (a2 + alpha * ax0);
+          At(k, k) = make_double2(-ph.x * alpha, -ph.y * alpha);
+        }
+      } else {
+        for (int i = k + lane; i < n; i += 32) Vh[i + (int64_t)k * n] = make_double2(0, 0);
+        if (lane == 0) sh_beta = 0.0;
+      }
+      for (int i = k + 1 + lane; i < n; i += 32) At(i, k) = make_double2(0, 0);
+      if (lane == 0) beta[k] = sh_beta;
+    }
+    __syncthreads();
+    const double b = sh_beta;
+    const double2 *v = Vh + (int64_t)k * n;
+    // A(k:n, j) -= beta v (v^dagger A(k:n, j)) for j > k, one warp per column; then the
+    // column's partial norm
+    for (int j = k + 1 + warp; j < n; j += nwarp) {
+      if (b != 0) {
+        double sx = 0, sy = 0;
+        for (int i = k + lane; i < n; i += 32) {
+          const double2 t = cmulc(v[i], At(i, j));   // conj(v_i) a_i
+          sx += t.x;
+          sy += t.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          sx += __shfl_xor_sync(0xffffffffu, sx, o);
+          sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        const double2 sb = make_double2(sx * b, sy * b);
+        for (int i = k + lane; i < n; i += 32) At(i, j) = csub(At(i, j), cmul(v[i], sb));
+        __syncwarp();
+      }
+      const double nj = vn1[j];
+      if (nj != 0) {
+        double t = cabsd(At(k, j)) / nj;
+        t = fmax(0.0, (1.0 + t) * (1.0 - t));
+        const double r = nj / vn2[j];
+        if (t * r * r <= tol3z) {
+          double q = 0;
+          for (int i = k + 1 + lane; i < n; i += 32) q += cabs2(At(i, j));
+          for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+          __syncwarp();
+          if (lane == 0) vn1[j] = vn2[j] = sqrt(q);
+        } else {
+          __syncwarp();
+          if (lane == 0) vn1[j] = nj * sqrt(t);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < n; j += kQrpThreads) perm[j] = sperm[j];
+}
+
+// X = R^dagger (lower triangular) from the upper triangle of R
+__global__ void k_rdagger(int n, const double2 *Rb, double2 *Xb) {
+  const int e = blockIdx.y;
+  const int64_t nn = (int64_t)n * n;
+  const double2 *R = Rb + e * nn;
+  double2 *X = Xb + e * nn;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nn;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    X[idx] = (j <= i) ? cconj(R[j + (int64_t)i * n]) : make_double2(0, 0);
+  }
+}
+
+// B <- Q B = H_0 (H_1 (... (H_{n-1} B))), one warp per column of B
+__global__ void __launch_bounds__(512) k_apply_q(int n, const double2 *Vhb, const double *betab, double2 *Bb) {
+  const int e = blockIdx.y;
+  const int64_t nn = (int64_t)n * n;
+  const double2 *Vh = Vhb + e * nn;
+  const double *beta = betab + (int64_t)e * n;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= n) return;
+  double2 *B = Bb + e * nn + (int64_t)j * n;
+  for (int k = n - 1; k >= 0; --k) {
+    const double b = beta[k];
+    if (b == 0) continue;
+    const double2 *v = Vh + (int64_t)k * n;
+    double sx = 0, sy = 0;
+    for (int i = k + lane; i < n; i += 32) {
+      const double2 t = cmulc(v[i], B[i]);
+      sx += t.x;
+      sy += t.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    const double2 sb = make_double2(sx * b, sy * b);
+    for (int i = k + lane; i < n; i += 32) B[i] = csub(B[i], cmul(v[i], sb));
+    __syncwarp();
+  }
+}
+
+// Out(perm[i], j) = In(i, j): the row permutation P In
+__global__ void k_permute_rows(int n, const int *permb, const double2 *Inb, double2 *Outb) {
+  const int e = blockIdx.y;
+  const int64_t nn = (int64_t)n * n;
+  const int *perm = permb + (int64_t)e * n;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nn;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    Outb[e * nn + perm[i] + (int64_t)j * n] = Inb[e * nn + idx];
+  }
+}
+
 
 __global__ void k_svd_init(int n, double2 *Wb) {
   const int e = blockIdx.y;
@@ -700,6 +898,29 @@ cbs_status launch_svd(int n_e, int n, double2 *A, double2 *W, double2 *U, double
   const int max_sweeps = 60;
   const int nn2 = (n + 1) & ~1;
   const int warps = kSvdThreads / 32;
+  const int64_t nn = (int64_t)n * n;
+  // workspace: reflectors (n x n), beta (n) and the pivot order (n) per energy
+  struct Work {
+    void *p = nullptr;
+    ~Work() { if (p) cudaFree(p); }
+  } wk;
+  const size_t wbytes = (size_t)nn * n_e * sizeof(double2) + (size_t)n * n_e * (sizeof(double) + sizeof(int)) + 256;
+  if (cudaMalloc(&wk.p, wbytes) != cudaSuccess) {
+    wk.p = nullptr;
+    set_error("cudaMalloc failed (SVD workspace)");
+    return CBS_ENOMEM;
+  }
+  double2 *Vh = (double2 *)wk.p;
+  double *beta = (double *)(Vh + nn * n_e);
+  int *perm = (int *)(beta + (size_t)n * n_e);
+  // T P = Q R in place (A holds R), X = R^dagger into Ws: the matrix the sweeps rotate
+  k_qrp<<<n_e, kQrpThreads, 0, st>>>(n, A, Vh, beta, perm);
+  cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  k_rdagger<<<dim3(64, (unsigned)n_e, 1), 256, 0, st>>>(n, A, Ws);
+  cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  double2 *X = Ws;
   dim3 grd_round((unsigned)ceil_div(nn2 / 2, warps), (unsigned)n_e, 1);
   k_svd_init<<<dim3(64, (unsigned)n_e, 1), 256, 0, st>>>(n, W);
   cbs::count_launches(1);
@@ -712,7 +933,7 @@ cbs_status launch_svd(int n_e, int n, double2 *A, double2 *W, double2 *U, double
   CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cudaError_t ce = cudaMemsetAsync(rot, 0, (size_t)n_e * sizeof(int), st);
   for (int r = 0; r < nn2 - 1 && ce == cudaSuccess; ++r) {
-    k_svd_round<<<grd_round, kSvdThreads, 0, st>>>(n, r, A, W, tolj, rot);
+    k_svd_round<<<grd_round, kSvdThreads, 0, st>>>(n, r, X, W, tolj, rot);
     cbs::count_launches(1);
     ce = cudaGetLastError();
   }
@@ -739,7 +960,14 @@ cbs_status launch_svd(int n_e, int n, double2 *A, double2 *W, double2 *U, double
   }
   cudaGraphExecDestroy(exec);
   if (status != CBS_OK) return status;
-  k_svd_finish<<<n_e, 1024, 0, st>>>(n, A, W, U, Ws, sig);
+  // X V_x = U_x Sigma: A <- U_x, U <- V_x (sorted); then U <- Q V_x, Ws <- P U_x
+  k_svd_finish<<<n_e, 1024, 0, st>>>(n, X, W, A, U, sig);
+  cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  k_apply_q<<<dim3((unsigned)ceil_div(n, 16), (unsigned)n_e, 1), 512, 0, st>>>(n, Vh, beta, U);
+  cbs::count_launches(1);
+  CBS_CUDA(cudaGetLastError());
+  k_permute_rows<<<dim3(64, (unsigned)n_e, 1), 256, 0, st>>>(n, perm, A, Ws);
   cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   // info: 1 if the sweep limit was reached (per energy: its last sweep still rotated)

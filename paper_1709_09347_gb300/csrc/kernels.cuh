@@ -16,7 +16,7 @@ cbs_status launch_moments(int n, int n_e, int n_w, int j0, int M, int64_t N, int
 int vhy_chunks(int64_t N);
 cbs_status launch_mu(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, const double2 *V,
                      const double2 *Y, const double2 *coef, double2 *part, double2 *mu,
-                     bool accumulate, int mirror, cudaStream_t st);
+                     bool accumulate, int mirror, bool v_real, cudaStream_t st);
 
 // dense.cu
 cbs_status launch_hankel(int n_e, int L, int M, const double2 *mu, double2 *T, double2 *Tl,

@@ -45,12 +45,33 @@ cbs_status launch_contour(int n_int, int M, double lambda_min, double2 *coef, do
 // mirror > 0: the solutions at the conjugate point j' = mirror - 1 - j (z_j' = conj(z_j),
 // same for the dual twists) are conj(Y_j), which holds for real blocks and a real V, and
 // enter with their own coefficients.
-template <int MM>
+template <int MM, bool MIR>
 __global__ void k_moments(int n, int n_w, int j0, int M, int64_t N, int L, const double2 *__restrict__ Y,
                           const double2 *__restrict__ coef, double2 *__restrict__ S, int accumulate,
                           int mirror) {
+  // MIR: a point and its conjugate enter together through
+  //   a y + a' conj(y) = (a + a') Re y + i (a - a') Im y,
+  // two complex-by-real products instead of two complex ones; the four combined
+  // coefficients of each (point, k) are formed once per block in shared memory.
+  extern __shared__ double2 mc[];   // [n_w][4][M]: a+a', i(a-a'), -(b+b'), -i(b-b')
   const int e = blockIdx.y, c = threadIdx.x, ly = threadIdx.y, py = blockDim.y;
   const int M2 = 2 * M;
+  if (MIR) {
+    for (int t = threadIdx.x + threadIdx.y * blockDim.x; t < n_w * M; t += blockDim.x * blockDim.y) {
+      const int jj = t / M, k = t % M;
+      const int jm = mirror - 1 - j0 - jj;
+      const double2 a = coef[((int64_t)(j0 + jj) * 2 + 0) * M2 + k];
+      const double2 b = coef[((int64_t)(j0 + jj) * 2 + 1) * M2 + k];
+      const double2 am = coef[((int64_t)jm * 2 + 0) * M2 + k];
+      const double2 bm = coef[((int64_t)jm * 2 + 1) * M2 + k];
+      double2 *q = mc + (int64_t)jj * 4 * M;
+      q[k] = make_double2(a.x + am.x, a.y + am.y);
+      q[M + k] = make_double2(-(a.y - am.y), a.x - am.x);
+      q[2 * M + k] = make_double2(-(b.x + bm.x), -(b.y + bm.y));
+      q[3 * M + k] = make_double2(b.y - bm.y, -(b.x - bm.x));
+    }
+    __syncthreads();
+  }
   const int64_t per = (int64_t)py * 4;
   const int64_t i0 = (int64_t)blockIdx.x * per;
   for (int64_t i = i0 + ly; i < min(N, i0 + per); i += py) {
@@ -63,24 +84,35 @@ __global__ void k_moments(int n, int n_w, int j0, int M, int64_t N, int L, const
       const int64_t s = (int64_t)e * n_w + jj;
       const double2 y1 = Y[(s * N + i) * L + c];
       const double2 y2 = Y[((n + s) * N + i) * L + c];
-      const double2 *a = coef + (int64_t)(j0 + jj) * 2 * M2;
-      const double2 *b = a + M2;
-#pragma unroll
-      for (int k = 0; k < MM; ++k)
-        if (k < M) {
-          acc[k] = cfma(a[k], y1, acc[k]);
-          acc[k] = cfma(make_double2(-b[k].x, -b[k].y), y2, acc[k]);
-        }
-      if (mirror > 0) {
-        const double2 *am = coef + (int64_t)(mirror - 1 - j0 - jj) * 2 * M2;
-        const double2 *bm = am + M2;
-        const double2 y1c = cconj(y1), y2c = cconj(y2);
+      if (MIR) {
+        const double2 *q = mc + (int64_t)jj * 4 * M;
 #pragma unroll
         for (int k = 0; k < MM; ++k)
           if (k < M) {
-            acc[k] = cfma(am[k], y1c, acc[k]);
-            acc[k] = cfma(make_double2(-bm[k].x, -bm[k].y), y2c, acc[k]);
+            const double2 p0 = q[k], p1 = q[M + k], p2 = q[2 * M + k], p3 = q[3 * M + k];
+            acc[k].x = fma(p3.x, y2.y, fma(p2.x, y2.x, fma(p1.x, y1.y, fma(p0.x, y1.x, acc[k].x))));
+            acc[k].y = fma(p3.y, y2.y, fma(p2.y, y2.x, fma(p1.y, y1.y, fma(p0.y, y1.x, acc[k].y))));
           }
+      } else {
+        const double2 *a = coef + (int64_t)(j0 + jj) * 2 * M2;
+        const double2 *b = a + M2;
+#pragma unroll
+        for (int k = 0; k < MM; ++k)
+          if (k < M) {
+            acc[k] = cfma(a[k], y1, acc[k]);
+            acc[k] = cfma(make_double2(-b[k].x, -b[k].y), y2, acc[k]);
+          }
+        if (mirror > 0) {
+          const double2 *am = coef + (int64_t)(mirror - 1 - j0 - jj) * 2 * M2;
+          const double2 *bm = am + M2;
+          const double2 y1c = cconj(y1), y2c = cconj(y2);
+#pragma unroll
+          for (int k = 0; k < MM; ++k)
+            if (k < M) {
+              acc[k] = cfma(am[k], y1c, acc[k]);
+              acc[k] = cfma(make_double2(-bm[k].x, -bm[k].y), y2c, acc[k]);
+            }
+        }
       }
     }
 #pragma unroll
@@ -93,11 +125,16 @@ cbs_status launch_moments(int n, int n_e, int n_w, int j0, int M, int64_t N, int
                           const double2 *coef, double2 *S, bool accumulate, int mirror, cudaStream_t st) {
   dim3 blk = col_block(L);
   dim3 grd((unsigned)ceil_div(N, (int64_t)blk.y * 4), (unsigned)n_e, 1);
-  if (M <= 8)
-    k_moments<8><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, accumulate ? 1 : 0, mirror);
-  else if (M <= 16)
-    k_moments<16><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, accumulate ? 1 : 0, mirror);
-  else {
+  const size_t msm = (size_t)n_w * 4 * M * sizeof(double2);
+  const bool mir = mirror > 0 && msm <= 48 * 1024;
+  const int acc = accumulate ? 1 : 0;
+  if (M <= 8) {
+    if (mir) k_moments<8, true><<<grd, blk, msm, st>>>(n, n_w, j0, M, N, L, Y, coef, S, acc, mirror);
+    else k_moments<8, false><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, acc, mirror);
+  } else if (M <= 16) {
+    if (mir) k_moments<16, true><<<grd, blk, msm, st>>>(n, n_w, j0, M, N, L, Y, coef, S, acc, mirror);
+    else k_moments<16, false><<<grd, blk, 0, st>>>(n, n_w, j0, M, N, L, Y, coef, S, acc, mirror);
+  } else {
     set_error("M must be <= 16");
     return CBS_EINVAL;
   }
@@ -106,9 +143,10 @@ cbs_status launch_moments(int n, int n_e, int n_w, int j0, int M, int64_t N, int
   return CBS_OK;
 }
 
-// part[s][chunk][c1][c2] = sum over the chunk's points of conj(V[i][c1]) Y[s][i][c2]
+// part[s][chunk][c1][c2] = sum over the chunk's points of conj(V[i][c1]) Y[s][i][c2];
+// RV: V is real (its imaginary parts are zero), two real products per term
 constexpr int kVhyTile = 16;
-template <int NQ>
+template <int NQ, bool RV>
 __global__ void k_vhy(int64_t N, int L, int n_chunks, const double2 *__restrict__ V,
                       const double2 *__restrict__ Y, double2 *__restrict__ part) {
   extern __shared__ double2 tile[];   // [kVhyTile][L] of V then of Y
@@ -134,7 +172,16 @@ __global__ void k_vhy(int64_t N, int L, int n_chunks, const double2 *__restrict_
       if (pidx < LL) {
         const int c1 = pidx / L, c2 = pidx % L;
         double2 a = acc[q];
-        for (int t = 0; t < cnt; ++t) a = cadd(a, cmulc(tv[t * L + c1], ty[t * L + c2]));
+        if (RV) {
+          for (int t = 0; t < cnt; ++t) {
+            const double v = tv[t * L + c1].x;
+            const double2 y = ty[t * L + c2];
+            a.x = fma(v, y.x, a.x);
+            a.y = fma(v, y.y, a.y);
+          }
+        } else {
+          for (int t = 0; t < cnt; ++t) a = cadd(a, cmulc(tv[t * L + c1], ty[t * L + c2]));
+        }
         acc[q] = a;
       }
     }
@@ -189,7 +236,7 @@ int vhy_chunks(int64_t N) {
 
 cbs_status launch_mu(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, const double2 *V,
                      const double2 *Y, const double2 *coef, double2 *part, double2 *mu,
-                     bool accumulate, int mirror, cudaStream_t st) {
+                     bool accumulate, int mirror, bool v_real, cudaStream_t st) {
   if (L > 64) {
     set_error("L must be <= 64 for the moment kernel");
     return CBS_EINVAL;
@@ -197,9 +244,15 @@ cbs_status launch_mu(int n, int n_e, int n_w, int j0, int M, int64_t N, int L, c
   const int nch = vhy_chunks(N);
   dim3 grd((unsigned)nch, (unsigned)(2 * n), 1);
   const size_t sm = 2 * kVhyTile * L * sizeof(double2);
-  if (L * L <= 4 * 256) k_vhy<4><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
-  else if (L * L <= 9 * 256) k_vhy<9><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
-  else k_vhy<16><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
+  if (v_real) {
+    if (L * L <= 4 * 256) k_vhy<4, true><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
+    else if (L * L <= 9 * 256) k_vhy<9, true><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
+    else k_vhy<16, true><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
+  } else {
+    if (L * L <= 4 * 256) k_vhy<4, false><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
+    else if (L * L <= 9 * 256) k_vhy<9, false><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
+    else k_vhy<16, false><<<grd, 256, sm, st>>>(N, L, nch, V, Y, part);
+  }
   cbs::count_launches(1);
   CBS_CUDA(cudaGetLastError());
   k_mu<<<dim3((unsigned)(2 * M), (unsigned)n_e, 1), 256, 0, st>>>(n, n_w, j0, 2 * M, L, nch, part,

@@ -747,7 +747,7 @@ static cbs_status solve_impl(const cbs_hamiltonian *h, const double *energies, i
       CBS_TRY(lap(&res->ms_solve));
       // ---- step 2: this wave's share of the moments
       CBS_TRY(launch_moments(nsys, ne, nwv, j0, M, N, L, S.Y, coef, Sm, j0 > 0, mirror ? n_int : 0, st));
-      CBS_TRY(launch_mu(nsys, ne, nwv, j0, M, N, L, dV, S.Y, coef, part, mu, j0 > 0, mirror ? n_int : 0, st));
+      CBS_TRY(launch_mu(nsys, ne, nwv, j0, M, N, L, dV, S.Y, coef, part, mu, j0 > 0, mirror ? n_int : 0, v_real, st));
       CBS_TRY(lap(&res->ms_moments));
     }
     // ---- step 3: extraction (Hankel SVD, reduced eigenproblem, vectors, residuals)
