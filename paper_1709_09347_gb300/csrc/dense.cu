@@ -588,6 +588,7 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
   __shared__ double rot_c[kMaxEigN];
   __shared__ double2 rot_s[kMaxEigN];
   __shared__ double sh_c;
+  __shared__ double2 sh_u1, sh_w1;
   __shared__ double2 sh_s;
   __shared__ int sh_defl[kEigThreads / 32];
   if (tid == 0) { sh_hi = m - 1; sh_fail = 0; }
@@ -658,36 +659,47 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(int ld, const int *mhat, do
       const double c = sh_c;
       const double2 sr = sh_s;
       if (tid == 0) { rot_c[k] = c; rot_s[k] = sr; }
-      // rows k, k+1 inside the window:  [a; b] <- [c a + s b; -conj(s) a + c b]
+      // the leader's entry of row k+2, untouched by this step's row rotation: in flight
+      // while the rows are rotated
+      double2 w2 = make_double2(0, 0);
+      if (tid == 0 && k + 2 <= hi) w2 = Aat(k + 2, k + 1);
+      // rows k, k+1 inside the window:  [a; b] <- [c a + s b; -conj(s) a + c b]; the new
+      // A(k+1, k) and A(k+1, k+1) also go to the leader through shared memory
       const int j0 = (k == l) ? l : k - 1;
       for (int j = j0 + tid; j <= hi; j += nt) {
         const double2 a = Aat(k, j), b = Aat(k + 1, j);
+        const double2 nb = csub(cscale(b, c), cmul(cconj(sr), a));
         Aat(k, j) = cadd(cscale(a, c), cmul(sr, b));
-        Aat(k + 1, j) = csub(cscale(b, c), cmul(cconj(sr), a));
+        Aat(k + 1, j) = nb;
+        if (j == k) sh_u1 = nb;
+        else if (j == k + 1) sh_w1 = nb;
       }
       __syncthreads();
-      // columns k, k+1 inside the window:  [u, w] <- [c u + conj(s) w, -s u + c w];
-      // thread 0 takes rows k+1 and k+2, whose column-k entries define the next rotation
-      const int i1 = min(k + 2, hi);
+      // columns k, k+1 inside the window:  [u, w] <- [c u + conj(s) w, -s u + c w].
+      // Thread 0 (alone in its warp here, so its chain does not wait for a divergent
+      // branch) takes rows k+1 and k+2, whose column-k entries define the next rotation;
+      // A(k+2, k) is zero before this rotation (the bulge sits one column to the left).
+      // Warps 1.. take rows l..k.
       if (tid == 0) {
         if (k > l) Aat(k + 1, k - 1) = make_double2(0, 0);   // the bulge the rotation removed
-        double2 xn = make_double2(0, 0), yn = make_double2(0, 0);
-        for (int i = k + 1; i <= i1; ++i) {
-          const double2 u = Aat(i, k), w = Aat(i, k + 1);
-          const double2 un = cadd(cscale(u, c), cmul(cconj(sr), w));
-          Aat(i, k) = un;
-          Aat(i, k + 1) = csub(cscale(w, c), cmul(sr, u));
-          if (i == k + 1) xn = un; else yn = un;
+        const double2 u = sh_u1, w = sh_w1;
+        const double2 xn = cadd(cscale(u, c), cmul(cconj(sr), w));
+        Aat(k + 1, k) = xn;
+        Aat(k + 1, k + 1) = csub(cscale(w, c), cmul(sr, u));
+        if (k + 2 <= hi) {
+          const double2 yn = cmul(cconj(sr), w2);
+          Aat(k + 2, k) = yn;
+          Aat(k + 2, k + 1) = cscale(w2, c);
+          if (k + 1 < hi) {
+            double cn;
+            double2 sn;
+            givens(xn, yn, cn, sn);
+            sh_c = cn;
+            sh_s = sn;
+          }
         }
-        if (k + 1 < hi) {
-          double cn;
-          double2 sn;
-          givens(xn, yn, cn, sn);
-          sh_c = cn;
-          sh_s = sn;
-        }
-      } else {
-        for (int i = l + tid - 1; i <= k; i += nt - 1) {
+      } else if (tid >= 32) {
+        for (int i = l + tid - 32; i <= k; i += nt - 32) {
           const double2 u = Aat(i, k), w = Aat(i, k + 1);
           Aat(i, k) = cadd(cscale(u, c), cmul(cconj(sr), w));
           Aat(i, k + 1) = csub(cscale(w, c), cmul(sr, u));
