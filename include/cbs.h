@@ -251,6 +251,24 @@ cbs_status cbs_solve(const cbs_hamiltonian *h, const double *energies, int n_e,
                      const cbs_contour *contour, int L, int M, const void *V,
                      const cbs_options *opt, cbs_result **out);
 
+/* The whole method for several cells of different sizes in one call (the paper distributes
+ * supercells and energies over its top and middle parallel layers, §3.3): cell c is solved
+ * exactly as cbs_solve(h[c], energies, n_e, contour, L, M, V[c], opt, &out[c]) would, on a
+ * stream and a host thread of its own (created by the call, on the calling thread's current
+ * device), so the cells' kernels interleave on the GPU; the call returns when every cell is
+ * done.  h: [n_cells] distinct handles (1 <= n_cells <= 64), not used by other work meanwhile;
+ * V: [n_cells] pointers, V[c] cell c's [N_c][L] complex128 block, host or device as in
+ * cbs_solve; opt->stream must be NULL; out: [n_cells] result handles (free each with
+ * cbs_result_free); cell_status: [n_cells] per-cell statuses, or NULL.
+ * Errors: CBS_EINVAL for bad arguments (nothing is run); if a cell fails with anything other
+ * than CBS_ENOCONV / CBS_EBREAKDOWN / CBS_WRANK, every out[c] is freed and NULL and that
+ * cell's status is returned (cbs_last_error() names the cell); otherwise the first non-OK
+ * status in cell order is returned, with every out[c] readable. */
+cbs_status cbs_solve_cells(const cbs_hamiltonian *const *h, int n_cells, const double *energies,
+                           int n_e, const cbs_contour *contour, int L, int M,
+                           const void *const *V, const cbs_options *opt, cbs_result **out,
+                           cbs_status *cell_status);
+
 /* Objective of the ring solves and its gradient (reverse mode, adjoint solves).
  * J = sum_{c=1,2} sum_j c_j^(c) ||Y_j^(c)||_F^2, with Y_j^(c) = P(z_j^(c))^{-1} V the solutions
  * of the shifted systems of §3.2 (Eq. (9)-(11)) at energy E, and real weights

@@ -29,7 +29,7 @@ EXPORTS = (
     "cbs_result_timing", "cbs_result_profile", "cbs_result_free", "cbs_last_error",
     "cbs_kernel_launches", "cbs_apply_workspace_size", "cbs_apply_ws", "cbs_apply_noalloc",
     "cbs_objective", "cbs_autotune_apply", "cbs_set_apply_shape",
-    "cbs_result_extract_timing", "cbs_hamiltonian_set_vloc",
+    "cbs_result_extract_timing", "cbs_hamiltonian_set_vloc", "cbs_solve_cells",
 )
 
 
@@ -96,6 +96,7 @@ def load():
     lib.cbs_apply.argtypes = [V, I, P(D), P(D), I, V, V, I, V]
     lib.cbs_solve_shifted.argtypes = [V, I, P(D), P(D), I, V, V, V, P(I), P(Options)]
     lib.cbs_solve.argtypes = [V, P(D), I, P(Contour), I, I, V, P(Options), P(V)]
+    lib.cbs_solve_cells.argtypes = [P(V), I, P(D), I, P(Contour), I, I, P(V), P(Options), P(V), P(I)]
     lib.cbs_result_count.argtypes = [V, I]
     lib.cbs_result_get.argtypes = [V, I, P(D), P(D), P(D), P(D)]
     lib.cbs_result_stats.argtypes = [V, I, P(Stats)]
@@ -314,6 +315,44 @@ def solve(H: Hamiltonian, energies, lambda_min, n_int, L, M, V, opts: Options | 
     finally:
         if h:
             lib.cbs_result_free(h)
+
+
+def solve_cells(Hs, energies, lambda_min, n_int, L, M, Vs, opts: Options | None = None,
+                allow=(CBS_OK, CBS_WRANK)):
+    """The whole method for several cells in one call (cbs_solve_cells: one stream and host
+    thread per cell).  Hs: distinct Hamiltonians; Vs: per cell [N_c, L] complex128, numpy
+    or CUDA tensors.  Returns (list of Result, list of per-cell statuses)."""
+    lib = load()
+    n = len(Hs)
+    assert len(Vs) == n and n >= 1
+    en = np.ascontiguousarray(np.atleast_1d(np.asarray(energies, float)))
+    ctr = Contour(float(lambda_min), int(n_int))
+    keep, ptrs = [], []
+    for V in Vs:
+        if isinstance(V, np.ndarray):
+            Vh = np.ascontiguousarray(V, dtype=np.complex128)
+            keep.append(Vh)
+            ptrs.append(Vh.ctypes.data)
+        else:
+            import torch
+            assert V.is_cuda and V.dtype == torch.complex128 and V.is_contiguous()
+            torch.cuda.current_stream().synchronize()
+            ptrs.append(V.data_ptr())
+    harr = (ct.c_void_p * n)(*[H.handle for H in Hs])
+    varr = (ct.c_void_p * n)(*ptrs)
+    outs = (ct.c_void_p * n)()
+    cst = (ct.c_int * n)()
+    o = opts or options()
+    st = lib.cbs_solve_cells(harr, n, _dptr(en), len(en), ct.byref(ctr), int(L), int(M), varr,
+                             ct.byref(o), outs, cst)
+    try:
+        _check(st, ok=tuple(allow) + (CBS_OK,))
+        return ([Result(outs[c], len(en), Hs[c].n, int(L), int(M), int(n_int), cst[c]) for c in range(n)],
+                [int(x) for x in cst])
+    finally:
+        for c in range(n):
+            if outs[c]:
+                lib.cbs_result_free(outs[c])
 
 
 def autotune_apply(H: Hamiltonian, n_sys: int, L: int, dtype) -> dict:

@@ -14,10 +14,20 @@ namespace cbs {
 
 static thread_local std::string g_err;
 static std::atomic<uint64_t> g_launches{0};
+// launches counted by the calling thread: what a graph capture brackets, exact also while
+// other threads (cbs_solve_cells) count their own
+static thread_local uint64_t t_launches = 0;
 
-void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
-void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
+void count_launches(uint64_t n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
+void uncount_launches(uint64_t n) {
+  g_launches.fetch_sub(n, std::memory_order_relaxed);
+  t_launches -= n;
+}
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+uint64_t thread_launches() { return t_launches; }
 
 void set_error(const std::string &msg) { g_err = msg; }
 

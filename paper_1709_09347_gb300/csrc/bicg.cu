@@ -537,12 +537,12 @@ cbs_status Bicg<R>::iterate(double tol, int max_iter, int check_every, cudaStrea
   if (!exec || exec_max_iter != max_iter || exec_check_every != check_every) {
     if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
     cudaGraph_t graph = nullptr;
-    const uint64_t c0 = launches_so_far();
+    const uint64_t c0 = thread_launches();
     CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cbs_status s = CBS_OK;
     for (int k = 0; k < check_every && s == CBS_OK; ++k) s = step(tol, max_iter, st, k);
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    exec_kernels = launches_so_far() - c0;
+    exec_kernels = thread_launches() - c0;
     uncount_launches(exec_kernels);
     if (s != CBS_OK) { if (graph) cudaGraphDestroy(graph); return s; }
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
@@ -904,12 +904,12 @@ cbs_status MultiShift<R>::iterate(int max_iter, int check_every, cudaStream_t st
   if (!exec || exec_max_iter != max_iter || exec_check_every != check_every) {
     if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
     cudaGraph_t graph = nullptr;
-    const uint64_t c0 = launches_so_far();
+    const uint64_t c0 = thread_launches();
     CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cbs_status s = CBS_OK;
     for (int k = 0; k < check_every && s == CBS_OK; ++k) s = step(max_iter, st, k);
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    exec_kernels = launches_so_far() - c0;
+    exec_kernels = thread_launches() - c0;
     uncount_launches(exec_kernels);
     if (s != CBS_OK) { if (graph) cudaGraphDestroy(graph); return s; }
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");

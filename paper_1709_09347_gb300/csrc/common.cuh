@@ -133,6 +133,7 @@ cbs_status cuda_fail(cudaError_t e, const char *what);
 void count_launches(uint64_t n);
 void uncount_launches(uint64_t n);   // kernels recorded into a graph, not run
 uint64_t launches_so_far();
+uint64_t thread_launches();   // this thread's share of launches_so_far()
 
 #define CBS_STR2(x) #x
 #define CBS_STR(x) CBS_STR2(x)

@@ -941,7 +941,7 @@ cbs_status launch_svd(int n_e, int n, double2 *A, double2 *W, double2 *U, double
   // capture one sweep
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  const uint64_t c0 = launches_so_far();
+  const uint64_t c0 = thread_launches();
   CBS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cudaError_t ce = cudaMemsetAsync(rot, 0, (size_t)n_e * sizeof(int), st);
   for (int r = 0; r < nn2 - 1 && ce == cudaSuccess; ++r) {
@@ -950,7 +950,7 @@ cbs_status launch_svd(int n_e, int n, double2 *A, double2 *W, double2 *U, double
     ce = cudaGetLastError();
   }
   cudaError_t ce2 = cudaStreamEndCapture(st, &graph);
-  const uint64_t per_sweep = launches_so_far() - c0;
+  const uint64_t per_sweep = thread_launches() - c0;
   uncount_launches(per_sweep);
   if (ce != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(ce, "SVD round capture"); }
   if (ce2 != cudaSuccess) return cuda_fail(ce2, "SVD sweep capture");

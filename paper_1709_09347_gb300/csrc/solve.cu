@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -959,6 +960,62 @@ extern "C" cbs_status cbs_solve(const cbs_hamiltonian *h, const double *energies
   }
   *out = res;
   return s;
+}
+
+// Several cells in one call: one host thread and one stream per cell, each running the
+// cbs_solve path, so that the cells' work interleaves on the device (one cell's extraction,
+// on one SM per energy, runs beside another cell's FP64 solves).
+extern "C" cbs_status cbs_solve_cells(const cbs_hamiltonian *const *h, int n_cells, const double *energies,
+                                      int n_e, const cbs_contour *contour, int L, int M,
+                                      const void *const *V, const cbs_options *opt, cbs_result **out,
+                                      cbs_status *cell_status) {
+  if (!out) { set_error("out is NULL"); return CBS_EINVAL; }
+  if (!h || !V || n_cells < 1 || n_cells > 64) {
+    set_error("cbs_solve_cells: bad argument (1 <= n_cells <= 64, h and V non-NULL)");
+    return CBS_EINVAL;
+  }
+  for (int c = 0; c < n_cells; ++c) out[c] = nullptr;
+  for (int c = 0; c < n_cells; ++c) {
+    if (!h[c] || !V[c]) { set_error("cbs_solve_cells: NULL Hamiltonian or V of a cell"); return CBS_EINVAL; }
+    for (int d = 0; d < c; ++d)
+      if (h[d] == h[c]) { set_error("cbs_solve_cells: a Hamiltonian handle appears twice"); return CBS_EINVAL; }
+  }
+  if (opt && opt->stream) {
+    set_error("cbs_solve_cells: every cell runs on a stream of its own; opt->stream must be NULL");
+    return CBS_EINVAL;
+  }
+  int dev = 0;
+  CBS_CUDA(cudaGetDevice(&dev));
+  std::vector<cbs_status> st((size_t)n_cells, CBS_OK);
+  std::vector<std::string> err((size_t)n_cells);
+  std::vector<std::thread> th;
+  th.reserve((size_t)n_cells);
+  for (int c = 0; c < n_cells; ++c)
+    th.emplace_back([&, c]() {
+      const cudaError_t ce = cudaSetDevice(dev);
+      if (ce != cudaSuccess) st[c] = cuda_fail(ce, "cudaSetDevice");
+      else st[c] = cbs_solve(h[c], energies, n_e, contour, L, M, V[c], opt, &out[c]);
+      if (st[c] != CBS_OK) err[c] = cbs_last_error();
+    });
+  for (auto &t : th) t.join();
+  if (cell_status)
+    for (int c = 0; c < n_cells; ++c) cell_status[c] = st[c];
+  auto soft = [](cbs_status x) { return x == CBS_OK || x == CBS_ENOCONV || x == CBS_EBREAKDOWN || x == CBS_WRANK; };
+  for (int c = 0; c < n_cells; ++c)
+    if (!soft(st[c])) {
+      for (int d = 0; d < n_cells; ++d) {
+        cbs_result_free(out[d]);
+        out[d] = nullptr;
+      }
+      set_error("cell " + std::to_string(c) + ": " + err[c]);
+      return st[c];
+    }
+  for (int c = 0; c < n_cells; ++c)
+    if (st[c] != CBS_OK) {
+      set_error("cell " + std::to_string(c) + ": " + err[c]);
+      return st[c];
+    }
+  return CBS_OK;
 }
 
 extern "C" int cbs_result_count(const cbs_result *r, int e) {

@@ -504,33 +504,84 @@ def test_conjugate_points(form):
     _compare(cplx.energies[0], ref, lam_tol)
 
 
-@pytest.mark.parametrize("name", ["c4a", "c4b", "c4c"])
-def test_solve_c4_cells_properties(name):
+def test_solve_c4_cells_properties():
     """The three uneven cells of the batching workload (48x48x12, 64x64x16, 96x96x20; 60, 120
     and 270 atoms; lambda_min = 0.5, N_int = 48, L = 24, M = 8) at E = 0.135 Ha, shifted family,
-    tolerance 1e-10, one call per cell: every solve reaches tol on its FP64 true residual,
-    every kept pair's residual recomputed with the oracle's explicit operator is <= 1e-8 and
-    equals the reported one, and the kept set is closed under conjugation and under
-    lambda -> 1/conj(lambda)."""
+    tolerance 1e-10, all three in one cbs_solve_cells call: every solve reaches tol on its FP64
+    true residual, every kept pair's residual recomputed with the oracle's explicit operator is
+    <= 1e-8 and equals the reported one, and the kept set is closed under conjugation and
+    under lambda -> 1/conj(lambda)."""
     need_gpu()
     from paper_1709_09347_gb300 import cbs
-    wl = synth.workload(name)
-    H = cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors)
-    E = float(wl.energies[40])
-    r = cbs.solve(H, [E], wl.lambda_min, wl.n_int, wl.L, wl.M, wl.V,
-                  cbs.options(tol=wl.tol, delta=wl.delta, multi_shift=1))
-    e = r.energies[0]
-    assert r.status in (cbs.CBS_OK, cbs.CBS_WRANK)
-    assert e["max_solve_residual"] <= wl.tol
-    if len(e["lam"]):
-        op = CellOperator(wl.grid, wl.vloc, wl.projectors)
-        rr = ss.residuals(op, E, e["lam"], e["vectors"], op.frobenius(E))
-        assert np.all(rr <= 1e-8)
-        assert np.allclose(rr, e["residual"], rtol=1e-5, atol=1e-15)
-        # closure holds to the accuracy 1e-10 solves give the Hankel extraction (up to
-        # 1.4e-6 measured on the 96x96x20 cell); the conjugation closure holds to rounding for a real V
-        assert np.max(_conj_defect(e["lam"]) / np.abs(e["lam"])) <= 1e-8
-        assert np.max(_closure_defect(e["lam"])) <= 1e-5
+    wls = [synth.workload(name) for name in ("c4a", "c4b", "c4c")]
+    Hs = [cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors) for wl in wls]
+    w0 = wls[0]
+    E = float(w0.energies[40])
+    res, st = cbs.solve_cells(Hs, [E], w0.lambda_min, w0.n_int, w0.L, w0.M, [wl.V for wl in wls],
+                              cbs.options(tol=w0.tol, delta=w0.delta, multi_shift=1))
+    for wl, r, sc in zip(wls, res, st):
+        e = r.energies[0]
+        assert sc in (cbs.CBS_OK, cbs.CBS_WRANK)
+        assert e["max_solve_residual"] <= wl.tol
+        if len(e["lam"]):
+            op = CellOperator(wl.grid, wl.vloc, wl.projectors)
+            rr = ss.residuals(op, E, e["lam"], e["vectors"], op.frobenius(E))
+            assert np.all(rr <= 1e-8)
+            assert np.allclose(rr, e["residual"], rtol=1e-5, atol=1e-15)
+            # closure holds to the accuracy 1e-10 solves give the Hankel extraction (up to
+            # 1.4e-6 measured on the 96x96x20 cell); the conjugation closure holds to rounding
+            # for a real V
+            assert np.max(_conj_defect(e["lam"]) / np.abs(e["lam"])) <= 1e-8
+            assert np.max(_closure_defect(e["lam"])) <= 1e-5
+
+
+def _two_tiny_cells():
+    a = synth.tiny_workload(nx=6, ny=5, nz=4, h=0.45, fd_order=4, n_atoms=2, r_c=0.8, sigma=0.3, L=8,
+                            energies=(0.2, 0.6))
+    b = synth.tiny_workload(nx=13, ny=10, nz=6, h=0.4, fd_order=12, n_atoms=4, r_c=1.1, sigma=0.4, L=8,
+                            energies=(0.2, 0.6), seed=12)
+    return a, b
+
+
+@pytest.mark.parametrize("form", [dict(multi_shift=1), dict(multi_shift=0, precision="fp32_refine")])
+def test_solve_cells_equals_single_calls(form):
+    """cbs_solve_cells on two cells of different sizes gives, cell by cell, exactly the
+    results of separate cbs_solve calls (same kernels on streams of their own)."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    cells = _two_tiny_cells()
+    Hs = [cbs.Hamiltonian(wl.grid, wl.vloc, wl.projectors) for wl in cells]
+    w0 = cells[0]
+    o = cbs.options(tol=1e-12, **form)
+    res, st = cbs.solve_cells(Hs, w0.energies, w0.lambda_min, w0.n_int, w0.L, w0.M, [wl.V for wl in cells], o)
+    for wl, H, r, sc in zip(cells, Hs, res, st):
+        single = cbs.solve(H, w0.energies, w0.lambda_min, w0.n_int, w0.L, w0.M, wl.V, o)
+        assert sc == single.status
+        for a, b in zip(r.energies, single.energies):
+            assert np.array_equal(a["lam"], b["lam"]) and np.array_equal(a["residual"], b["residual"])
+            assert np.array_equal(a["vectors"], b["vectors"])
+            assert a["rank"] == b["rank"] and a["flags"] == b["flags"]
+
+
+def test_solve_cells_failures():
+    """A cell that fails hard (a non-finite V) fails the call and names the cell, with no
+    result kept; a handle given twice and a caller stream are rejected before anything runs."""
+    need_gpu()
+    from paper_1709_09347_gb300 import cbs
+    a, b = _two_tiny_cells()
+    Ha = cbs.Hamiltonian(a.grid, a.vloc, a.projectors)
+    Hb = cbs.Hamiltonian(b.grid, b.vloc, b.projectors)
+    bad = b.V.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(cbs.CbsError) as ex:
+        cbs.solve_cells([Ha, Hb], a.energies, a.lambda_min, a.n_int, a.L, a.M, [a.V, bad], cbs.options())
+    assert ex.value.status == cbs.CBS_EINVAL and "cell 1" in str(ex.value)
+    with pytest.raises(cbs.CbsError):
+        cbs.solve_cells([Ha, Ha], a.energies, a.lambda_min, a.n_int, a.L, a.M, [a.V, a.V], cbs.options())
+    # the library stays usable
+    res, st = cbs.solve_cells([Ha, Hb], a.energies, a.lambda_min, a.n_int, a.L, a.M, [a.V, b.V],
+                              cbs.options(tol=1e-12))
+    assert len(res) == 2 and all(x in (cbs.CBS_OK, cbs.CBS_WRANK) for x in st)
 
 
 def test_c5_operator_and_waves():
